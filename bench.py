@@ -1,0 +1,362 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the GB300 Lomb-Scargle path.
+
+A step is one pass of the whole path over one batch resident in HBM: the
+prologue (centring, phase records), the work-queue order, the persistent
+trig-sum kernel with its fused power/argmax epilogue and the finalize
+kernel, replayed as one CUDA graph (``lsp_plan_execute``).  The default
+workload is the ragged survey batch: 10000 objects, N_t uniform in
+[50, 500] with a seasonal cadence, N_f = 100000 on [0.24, 12) c/d, FP32 sums
+with FP64/fixed-point phases, argmax only.
+
+One JSON line is printed by rank 0.  ``value`` is objects/s over all ranks
+(weak scaling: every rank runs its own batch of the same shape); ``e2e`` is
+the same metric through the host-buffer entry point with the copies inside
+the timed region; ``roofline`` relates the main kernel's measured pair rate
+to the FP32-pipe bound; ``cpu_baseline`` times the FP64 CPU oracle on a
+bounded sample of the same workload on this host's cores.
+
+``--impl reference`` times the oracle alone (the CPU reference arm).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "objects/sec and trig-sum evals/s (N_t*N_f) vs FP32 roofline; learned vs plain"
+FP32_OPS_PER_PAIR = 8      # 2 FMUL + 2 FFMA (rotation) + 4 FFMA (XC, XS, CC, CS)
+FP32_LANES_PER_SM = 128    # FP32 lanes per SM per clock
+
+WORKLOADS = {
+    "ragged_survey": dict(kind="batch", top_k=1, power=False, cpu_sample=64, ref_per_step=6,
+                          desc="10000 objects, N_t~U{50..500}, seasonal cadence, N_f=1e5 on [0.24,12) c/d, argmax only"),
+    "ragged_lognormal": dict(kind="batch", top_k=3, power=False, cpu_sample=48, ref_per_step=6,
+                             desc="100000 objects, N_t log-uniform in [10,2000], N_f=5e4 on [0.24,12) c/d, argmax + top-3"),
+    "single_small": dict(kind="single", top_k=1, power=True, cpu_sample=1, ref_per_step=1,
+                         desc="1 object, N_t=1000, N_f=1e5 on [0.1,10) c/d, full power + argmax"),
+    "single_large": dict(kind="single", top_k=1, power=True, cpu_sample=1, ref_per_step=1,
+                         desc="1 object, N_t=1e5, N_f=1e6 on [0.05,25) c/d, full power + argmax"),
+}
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
+            int(os.environ.get("LOCAL_RANK", 0)))
+
+
+def make_workload(name, rank):
+    seed = synth.SEEDS[name] + 1_000_003 * rank
+    return synth.by_name(name, seed=seed)
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi samples every 200 ms while the timed region runs."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu_index = gpu_index
+        self.rows = []
+        self.proc = None
+        self.t0 = self.t1 = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.gpu_index)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+        time.sleep(0.3)
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append((time.time(), [x.strip() for x in line.split(",")]))
+
+    def mark(self, which):
+        if which == 0:
+            self.t0 = time.time()
+        else:
+            self.t1 = time.time()
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = [r for (ts, r) in self.rows if self.t0 - 0.25 <= ts <= self.t1 + 0.25 and len(r) >= 9]
+        if not rows:
+            rows = [r for (_, r) in self.rows if len(r) >= 9]
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        power = [float(r[3]) for r in rows if r[3].replace(".", "").isdigit()]
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows), "power_w_max": max(power) if power else None}
+
+
+def source_hash():
+    h = hashlib.sha256()
+    for f in ("lsp_main_impl.cuh", "lsp_common.cuh", "lsp_main_f32.cu"):
+        with open(os.path.join(ROOT, "paper_2105_04006_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(workload, src_hash):
+    """DRAM bytes per main-kernel launch from the committed ncu summary, if it is current."""
+    path = os.path.join(ROOT, "profiles", "main_kernel_traffic.md")
+    if not os.path.exists(path):
+        return None
+    for line in open(path):
+        if line.startswith("| " + workload + " |"):
+            cells = [c.strip() for c in line.strip().strip("|").split("|")]
+            # | workload | source hash | bytes per launch (full workload) | ...
+            if len(cells) >= 3 and cells[1] == src_hash:
+                try:
+                    return float(cells[2])
+                except ValueError:
+                    return None
+    return None
+
+
+# ------------------------------------------------------------- CPU baseline
+def cpu_baseline(b, n_sample, top_k):
+    import oracle
+    oracle.build()
+    n_sample = min(n_sample, b.n_obj)
+    if b.n_obj == 1:
+        sub, what = b, "the whole object"
+    else:
+        idx = np.linspace(0, b.n_obj - 1, n_sample).astype(np.int64)
+        sub, what = b.subset(idx), f"{n_sample} objects evenly spaced over the batch"
+    g = b.grid
+    t0 = time.perf_counter()
+    oracle.lsp_batch(sub.t, sub.y.astype(np.float32).astype(np.float64), sub.offsets, g.f_min, g.f_max,
+                     g.n_f, top_k=top_k, return_power=False)
+    dt = time.perf_counter() - t0
+    return {"value": sub.n_obj / dt, "unit": "objects/s", "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"{what} ({sub.pairs:.3g} pairs, FP64 two-scan Eq. 1-2), {dt:.1f} s",
+            "pairs_per_s": sub.pairs / dt}
+
+
+def run_reference(args, w, name):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.build()
+    b = make_workload(name, 0)
+    per = w["ref_per_step"]
+    g = b.grid
+    steps_t = []
+
+    def step(i):
+        if b.n_obj == 1:
+            sub = b
+        else:
+            lo = (i * per) % max(1, b.n_obj - per)
+            sub = b.subset(np.arange(lo, lo + per))
+        t0 = time.perf_counter()
+        oracle.lsp_batch(sub.t, sub.y.astype(np.float32).astype(np.float64), sub.offsets, g.f_min, g.f_max,
+                         g.n_f, top_k=w["top_k"], return_power=w["power"])
+        return time.perf_counter() - t0, sub.n_obj
+
+    for i in range(args.warmup):
+        step(i)
+    n_done = 0
+    for i in range(args.steps):
+        dt, n = step(args.warmup + i)
+        steps_t.append(dt)
+        n_done += n
+    total = sum(steps_t)
+    value = n_done / total
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "objects/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": name, "shape": w["desc"],
+                                        "sample_per_step": f"{per} objects" if b.n_obj > 1 else "whole object"},
+        "cpu_baseline": {"value": value, "unit": "objects/s", "cores": oracle.num_threads(), "kind": "oracle",
+                         "sample": f"{per if b.n_obj > 1 else 1} objects per step, {args.steps} steps"},
+        "e2e": {"value": value, "unit": "objects/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# --------------------------------------------------------------- GPU arm
+def run_gpu(args, w, name):
+    import torch
+    import paper_2105_04006_gb300 as lsp
+
+    rank, world, local = dist_env()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    b = make_workload(name, rank)
+    g = lsp.Grid(b.grid.f_min, b.grid.f_max, b.grid.n_f)
+    t = torch.tensor(b.t, dtype=torch.float64, device=dev)
+    y = torch.tensor(b.y.astype(np.float32), device=dev)
+    off = torch.tensor(b.offsets, dtype=torch.int64, device=dev) if b.n_obj > 1 else None
+    power = torch.empty((b.n_obj, g.n_f), dtype=torch.float32, device=dev) if w["power"] else None
+    plan = lsp.Plan(b.n_obj, b.t.size, g, top_k=w["top_k"])
+    if not args.no_tune:
+        cache = os.path.join(ROOT, "paper_2105_04006_gb300", "_build", "tune_cache.jsonl")
+        plan.autotune(t, y, off, cache_path=cache)
+    plan.enable_timing(True)
+    peaks = plan.peaks_buffer(dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > 129 MB L2
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        plan.execute(t, y, off, power=power, peaks=peaks)
+    barrier()
+    gpu_index = (os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",")[local]
+                 if os.environ.get("CUDA_VISIBLE_DEVICES") else str(local))
+    clk = ClockSampler(gpu_index)
+    clk.start()
+    barrier()
+    clk.mark(0)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    main_ms = []
+    for i in range(args.steps):
+        flush.fill_(i & 0xFF)
+        ev[i][0].record()
+        plan.execute(t, y, off, power=power, peaks=peaks)
+        ev[i][1].record()
+        main_ms.append(plan.main_kernel_ms())
+    barrier()
+    clk.mark(1)
+    clocks = clk.stop()
+    step_ms = [a.elapsed_time(c) for a, c in ev]
+    total_s = torch.tensor([sum(step_ms) / 1e3], dtype=torch.float64, device=dev)
+    if dist is not None:
+        dist.all_reduce(total_s, op=dist.ReduceOp.MAX)
+    total_s = float(total_s.item())
+    value = world * b.n_obj * args.steps / total_s
+    pairs = b.pairs
+
+    # end to end through the host-buffer entry point (pinned host memory)
+    th = torch.from_numpy(b.t).pin_memory()
+    yh = torch.from_numpy(b.y.astype(np.float32)).pin_memory()
+    oh = torch.from_numpy(b.offsets).pin_memory() if b.n_obj > 1 else None
+    ph = torch.empty((b.n_obj, g.n_f), dtype=torch.float32).pin_memory() if w["power"] else None
+    pk_host = np.empty(b.n_obj * w["top_k"], dtype=lsp.PEAK_DTYPE)
+    plan.enable_timing(False)
+    plan.execute_host(th, yh, oh, power=ph, peaks=pk_host)  # warm: allocates staging, captures
+    barrier()
+    e2e_ms = []
+    for i in range(args.steps):
+        flush.fill_(i & 0xFF)
+        a, c = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        plan.execute_host(th, yh, oh, power=ph, peaks=pk_host)
+        c.record()
+        c.synchronize()
+        e2e_ms.append(a.elapsed_time(c))
+    e2e_s = torch.tensor([sum(e2e_ms) / 1e3], dtype=torch.float64, device=dev)
+    if dist is not None:
+        dist.all_reduce(e2e_s, op=dist.ReduceOp.MAX)
+    e2e_value = world * b.n_obj * args.steps / float(e2e_s.item())
+    h2d = th.numel() * 8 + yh.numel() * 4 + (oh.numel() * 8 if oh is not None else 0)
+    d2h = pk_host.nbytes + (ph.numel() * 4 if ph is not None else 0)
+
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    main_avg = statistics.mean(main_ms)
+    achieved = pairs / (main_avg / 1e3) / 1e9
+    clk_mhz = (clocks or {}).get("sm_mhz") or 0.0
+    peak = n_sm * FP32_LANES_PER_SM * clk_mhz * 1e6 / FP32_OPS_PER_PAIR / 1e9 if clk_mhz else None
+    peak_max = n_sm * FP32_LANES_PER_SM * 2070e6 / FP32_OPS_PER_PAIR / 1e9
+    src = source_hash()
+    traffic = recorded_traffic(name, src)
+
+    line = None
+    if rank == 0:
+        cpu = None if args.no_cpu else cpu_baseline(b, w["cpu_sample"], w["top_k"])
+        line = {
+            "impl": "gb300", "metric": METRIC, "value": value, "unit": "objects/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": statistics.mean(step_ms),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": name, "shape": w["desc"], "n_obj": b.n_obj, "total_nt": int(b.t.size),
+                       "n_f": g.n_f, "precision": "fp32 sums, fp64/fixed-point phase",
+                       "l2": "flushed between steps (256 MiB write)", "kernel_config": plan.config},
+            "pairs_per_s": world * pairs * args.steps / total_s,
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gpair/s",
+                         "frac": (achieved / peak) if peak else None, "traffic": traffic,
+                         "kernel": "main trig-sum kernel", "main_kernel_ms": main_avg,
+                         "peak_basis": f"{n_sm} SMs x {FP32_LANES_PER_SM} FP32 lanes x sampled SM clock "
+                                       f"/ {FP32_OPS_PER_PAIR} FP32 ops per pair",
+                         "peak_at_max_clock": peak_max, "source_hash": src},
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": "objects/s", "h2d_bytes_per_step": int(h2d),
+                    "d2h_bytes_per_step": int(d2h), "ms_per_step": statistics.mean(e2e_ms)},
+            "gpu_launches": plan.kernel_count * args.steps,
+            "clocks": clocks,
+        }
+    plan.close()
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    if line is not None:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="ragged_survey")
+    ap.add_argument("--no-tune", action="store_true", help="use the default kernel configuration")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    w = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        return run_reference(args, w, args.workload)
+    return run_gpu(args, w, args.workload)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

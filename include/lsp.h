@@ -1,0 +1,233 @@
+/*
+ * lsp.h -- C ABI of the GB300 (sm_103a) Lomb-Scargle periodogram library.
+ *
+ * The library computes the direct O(N_t * N_f) Lomb-Scargle periodogram of
+ * Gowanlock et al. (arXiv:2105.04006) for one light curve or for a ragged
+ * batch of light curves, and the period given by each periodogram's maximum.
+ *
+ *   Section 2, Eq. 1:  tan(2 w tau) = sum_j sin(2 w t_j) / sum_j cos(2 w t_j)
+ *   Section 2, Eq. 2:  P(f) = 1/2 ( [sum_j y_j cos w(t_j-tau)]^2 / sum_j cos^2 w(t_j-tau)
+ *                                 + [sum_j y_j sin w(t_j-tau)]^2 / sum_j sin^2 w(t_j-tau) )
+ *   with w = 2 pi f, y the zero-mean magnitudes (Section 2), and the
+ *   half-open grid f_k = f_min + k (f_max - f_min)/N_f, k = 0..N_f-1 (Section 2).
+ *
+ * Conventions shared by every entry point:
+ *   - Frequencies are in cycles per unit of t (e.g. cycles/day); the period
+ *     of bin k is 1/f_k.  (The paper's grid is angular, w = 2 pi f.)
+ *   - Unless stated otherwise, array arguments are DEVICE pointers owned by
+ *     the caller; the library never frees them and never keeps them past
+ *     the call (plans keep nothing either, except what lsp_plan_execute
+ *     captured into a CUDA graph, see there).
+ *   - Every compute entry point is asynchronous on `stream` (0 = the legacy
+ *     default stream) and performs no device allocation: scratch memory is
+ *     the caller's `workspace` (size from lsp_workspace_size) or a plan's.
+ *   - Arguments are validated on the host before anything is launched; a
+ *     failure returns a nonzero lsp_status, launches nothing, and leaves a
+ *     message for lsp_last_error() (per calling thread).
+ *   - Problems of one object (fewer than two observations, zero variance,
+ *     NaN/Inf input) do not fail the call: that object gets power 0,
+ *     idx -1 and a nonzero lsp_peak.flags.
+ *   - Results are deterministic: two calls with the same inputs and options
+ *     give bit-identical outputs.  Ties of the maximum go to the lowest
+ *     frequency index (the first maximum, Section 3.3).
+ */
+#ifndef LSP_H
+#define LSP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* A cudaStream_t (the CUDA runtime's stream handle); 0 = legacy default stream. */
+typedef struct CUstream_st* lsp_stream_t;
+
+typedef enum lsp_status {
+  LSP_OK = 0,
+  LSP_E_ARG = 1,         /* invalid argument; nothing was launched */
+  LSP_E_CUDA = 2,        /* a CUDA runtime call failed (launch, copy, graph) */
+  LSP_E_NOMEM = 3,       /* a plan could not allocate its device memory */
+  LSP_E_WORKSPACE = 4,   /* the caller's workspace is smaller than required */
+  LSP_E_NUMERIC = 5,     /* reserved: per-object problems go to lsp_peak.flags */
+  LSP_E_TIMEOUT = 6,     /* a bounded device-side wait gave up */
+  LSP_E_UNSUPPORTED = 7  /* a valid request this build does not implement */
+} lsp_status;
+
+typedef enum lsp_precision {
+  LSP_FP32 = 0, /* trig sums in FP32; phases reduced in FP64 / fixed point (y, power: float) */
+  LSP_FP64 = 1  /* everything in FP64 (y, power: double) */
+} lsp_precision;
+
+typedef enum lsp_norm {
+  LSP_NORM_PSD = 0,      /* P of Eq. 2, in units of y^2 */
+  LSP_NORM_STANDARD = 1  /* P_n = 2 P / sum_j (y_j - mean)^2, in [0, 1] */
+} lsp_norm;
+
+/* Per-object flags (lsp_peak.flags). */
+#define LSP_FLAG_FEW_OBS 1     /* fewer than two observations */
+#define LSP_FLAG_ZERO_VAR 2    /* the (centred) magnitudes are all zero */
+#define LSP_FLAG_NONFINITE 4   /* a NaN or Inf in the object's t or y */
+#define LSP_FLAG_BAD_OFFSETS 8 /* offsets[o+1] < offsets[o] or outside [0, total_nt] */
+
+/* Half-open evenly spaced grid [f_min, f_max) of n_f frequencies (Section 2). */
+typedef struct lsp_grid {
+  double f_min; /* > 0 (Eq. 1 divides by 2w) */
+  double f_max; /* > f_min */
+  int64_t n_f;  /* >= 1 */
+} lsp_grid;
+
+/* Options.  Zero-initialise and set what you need, or use lsp_default_opts(). */
+typedef struct lsp_opts {
+  int32_t precision;     /* lsp_precision (default LSP_FP32) */
+  int32_t norm;          /* lsp_norm (default LSP_NORM_STANDARD) */
+  int32_t center_y;      /* nonzero: subtract each object's mean of y, in FP64 (default 1) */
+  int32_t top_k;         /* peaks per object, 1..3 (default 1); 2..3 = largest local maxima */
+  int32_t k_reseed;      /* frequencies between exact sin/cos reseeds; 0 = tuned default */
+  int32_t freqs_per_thread; /* frequencies per thread (multiple of k_reseed); 0 = tuned default */
+  int32_t block_threads; /* threads per CTA of the main kernel (64..256, /32); 0 = default */
+  int32_t obs_split;     /* single object: N_t split over this many CTAs; 0 = auto */
+} lsp_opts;
+
+/* One peak.  For top_k = 1 it is the periodogram's first maximum. */
+typedef struct lsp_peak {
+  int64_t idx;    /* grid index, -1 if the object has none (flags != 0) */
+  double power;   /* power at idx in the requested normalisation */
+  double freq;    /* f_min + idx (f_max - f_min)/n_f */
+  double period;  /* 1 / freq */
+  int32_t flags;  /* LSP_FLAG_* of the object */
+  int32_t reserved;
+} lsp_peak; /* 40 bytes */
+
+/* ---- status ------------------------------------------------------------ */
+
+const char* lsp_status_string(lsp_status status);
+/* Text of the last failure in the calling thread ("" if none). */
+const char* lsp_last_error(void);
+lsp_opts lsp_default_opts(void);
+/* Library version, as major*10000 + minor*100 + patch. */
+int32_t lsp_version(void);
+
+/* ---- one-shot entry points -------------------------------------------- */
+
+/*
+ * Bytes of device workspace that lsp_periodogram (n_obj = 1) or lsp_batch
+ * need for this shape and options.  Writes *bytes; never launches anything.
+ */
+lsp_status lsp_workspace_size(int64_t n_obj, int64_t total_nt, const lsp_grid* grid,
+                              const lsp_opts* opts, size_t* bytes);
+
+/*
+ * Single-object mode (Section 3.3).  t[n_t] (double) and y[n_t] (float for
+ * LSP_FP32, double for LSP_FP64) hold one light curve, in any time order.
+ * power_out (nullable) receives n_f powers of the precision's type -- the
+ * paper's "return the periodogram or not" option; leaving it NULL keeps the
+ * periodogram out of HBM entirely.  peaks (nullable) receives opts->top_k
+ * lsp_peak entries.  workspace must hold lsp_workspace_size(1, n_t, ...)
+ * bytes and be 256-byte aligned; the call may use all of it.
+ */
+lsp_status lsp_periodogram(const double* t, const void* y, int64_t n_t, const lsp_grid* grid,
+                           const lsp_opts* opts, void* power_out, lsp_peak* peaks,
+                           void* workspace, size_t ws_bytes, lsp_stream_t stream);
+
+/*
+ * Batch mode (Section 3.4) over a CSR layout: object o owns
+ * t/y[offsets[o] .. offsets[o+1]), offsets has n_obj + 1 int64 entries with
+ * offsets[0] = 0 and offsets[n_obj] = total_nt (device array; a violated
+ * entry flags the objects it touches with LSP_FLAG_BAD_OFFSETS instead of
+ * being read out of bounds).  All objects share one grid.  power_out
+ * (nullable) is n_obj x n_f, row-major; peaks (nullable) is n_obj x top_k.
+ * One launch sequence covers the whole batch: a prologue, a persistent
+ * main kernel that pulls (object, frequency-chunk) items from a queue
+ * ordered by decreasing N_t, and a finalize kernel.
+ */
+lsp_status lsp_batch(const double* t, const void* y, const int64_t* offsets, int64_t n_obj,
+                     int64_t total_nt, const lsp_grid* grid, const lsp_opts* opts,
+                     void* power_out, lsp_peak* peaks, void* workspace, size_t ws_bytes,
+                     lsp_stream_t stream);
+
+/*
+ * Period of stored periodograms (Section 3.3's separate argmax step):
+ * power is n_obj x n_f of type float (LSP_FP32) or double (LSP_FP64); each
+ * row's first maximum is written to peaks[o] (idx, power, freq, period;
+ * flags 0).  NaN entries are never selected.  No workspace is needed.
+ */
+lsp_status lsp_argmax_period(const void* power, int64_t n_obj, int64_t n_f, const lsp_grid* grid,
+                             int32_t precision, lsp_peak* peaks, lsp_stream_t stream);
+
+/* ---- plans: tuned, graph-captured repeats ------------------------------ */
+
+typedef struct lsp_plan lsp_plan;
+
+/* The launch configuration a plan uses (see lsp_plan_autotune). */
+typedef struct lsp_config {
+  int32_t k_reseed;
+  int32_t freqs_per_thread;
+  int32_t block_threads;
+  int32_t obs_split;
+  int32_t packed;      /* 1: packed f32x2 arithmetic across two reseed chains */
+  int32_t reserved[3];
+} lsp_config;
+
+/*
+ * A plan owns a workspace (and staging buffers for the host entry point,
+ * allocated by its first call) for one shape: n_obj objects (1 = single-
+ * object mode) with total_nt observations on `grid`.  lsp_plan_execute
+ * never allocates.
+ */
+lsp_status lsp_plan_create(lsp_plan** plan, int64_t n_obj, int64_t total_nt, const lsp_grid* grid,
+                           const lsp_opts* opts);
+
+/*
+ * Run the plan on device inputs (offsets may be NULL when n_obj == 1).
+ * The launch sequence is captured into a CUDA graph on the first call and
+ * replayed afterwards while the pointer arguments stay the same (a change
+ * re-captures).  Do not make the first call inside another stream capture.
+ */
+lsp_status lsp_plan_execute(lsp_plan* plan, const double* t, const void* y, const int64_t* offsets,
+                            void* power_out, lsp_peak* peaks, lsp_stream_t stream);
+
+/*
+ * End-to-end variant on HOST buffers: copies t, y, offsets to the device,
+ * runs the plan, copies the peaks (and the periodogram when power_out is
+ * not NULL) back, and synchronises `stream` before returning.  Pinned host
+ * memory gives the fastest copies.  The first call allocates the plan's
+ * device staging buffers (later calls reuse them).
+ */
+lsp_status lsp_plan_execute_host(lsp_plan* plan, const double* t, const void* y,
+                                 const int64_t* offsets, void* power_out, lsp_peak* peaks,
+                                 lsp_stream_t stream);
+
+/*
+ * Measure the candidate launch configurations on these inputs, keep the
+ * fastest one whose powers stay within the FP32 error gate (1e-4 absolute
+ * in P_n, against the FP64 path on sampled frequencies), and use it from
+ * now on.  Synchronises `stream`.  When cache_path is not NULL the choice
+ * is read from / appended to that JSON-lines file, keyed by device, shape
+ * class and options.
+ */
+lsp_status lsp_plan_autotune(lsp_plan* plan, const double* t, const void* y, const int64_t* offsets,
+                             const char* cache_path, lsp_stream_t stream);
+
+/*
+ * Timing probe.  While enabled, each execution of the plan also records two
+ * CUDA events on its stream, around the main (trig-sum) kernel, inside the
+ * captured graph.  lsp_plan_main_kernel_ms waits for the last execution's
+ * second event and returns the main kernel's duration in milliseconds.
+ * Enabling or disabling re-captures the graph on the next execution.
+ */
+lsp_status lsp_plan_enable_timing(lsp_plan* plan, int32_t enable);
+lsp_status lsp_plan_main_kernel_ms(lsp_plan* plan, float* ms);
+/* Number of the library's kernels one execution of the plan launches. */
+lsp_status lsp_plan_kernel_count(const lsp_plan* plan, int32_t* count);
+
+lsp_status lsp_plan_get_config(const lsp_plan* plan, lsp_config* config);
+lsp_status lsp_plan_set_config(lsp_plan* plan, const lsp_config* config);
+void lsp_plan_destroy(lsp_plan* plan);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LSP_H */

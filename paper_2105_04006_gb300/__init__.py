@@ -1,0 +1,354 @@
+"""Python binding of the GB300 Lomb-Scargle library (``include/lsp.h``).
+
+Argument marshalling only: every step of the periodogram runs in the CUDA
+library ``_build/liblsp.so`` (built by ``paper_2105_04006_gb300.build``).
+PyTorch supplies device memory and the current stream.  If the library is
+missing, importing works but every call raises ``LibraryNotBuilt`` -- there
+is no CPU fallback.
+
+Names follow the C ABI: ``periodogram`` (single object, Section 3.3),
+``batch`` (ragged CSR batch, Section 3.4), ``argmax_period`` (the period of a
+stored periodogram), ``Plan`` (tuned, graph-captured repeats).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "liblsp.so")
+
+FP32, FP64 = 0, 1
+NORM_PSD, NORM_STANDARD = 0, 1
+FLAG_FEW_OBS, FLAG_ZERO_VAR, FLAG_NONFINITE, FLAG_BAD_OFFSETS = 1, 2, 4, 8
+
+PEAK_DTYPE = np.dtype([("idx", "<i8"), ("power", "<f8"), ("freq", "<f8"), ("period", "<f8"),
+                       ("flags", "<i4"), ("reserved", "<i4")])
+assert PEAK_DTYPE.itemsize == 40
+
+
+class LibraryNotBuilt(RuntimeError):
+    pass
+
+
+class LSPError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"lsp status {status}: {message}")
+        self.status = status
+
+
+class Grid(ctypes.Structure):
+    """Half-open grid [f_min, f_max) of n_f frequencies (cycles per unit of t)."""
+    _fields_ = [("f_min", ctypes.c_double), ("f_max", ctypes.c_double), ("n_f", ctypes.c_int64)]
+
+    @property
+    def df(self) -> float:
+        return (self.f_max - self.f_min) / float(self.n_f)
+
+    def freqs(self) -> np.ndarray:
+        return self.f_min + np.arange(self.n_f, dtype=np.float64) * self.df
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int32), ("norm", ctypes.c_int32), ("center_y", ctypes.c_int32),
+                ("top_k", ctypes.c_int32), ("k_reseed", ctypes.c_int32),
+                ("freqs_per_thread", ctypes.c_int32), ("block_threads", ctypes.c_int32),
+                ("obs_split", ctypes.c_int32)]
+
+
+class Config(ctypes.Structure):
+    _fields_ = [("k_reseed", ctypes.c_int32), ("freqs_per_thread", ctypes.c_int32),
+                ("block_threads", ctypes.c_int32), ("obs_split", ctypes.c_int32),
+                ("packed", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+
+    def as_dict(self):
+        return dict(k_reseed=self.k_reseed, freqs_per_thread=self.freqs_per_thread,
+                    block_threads=self.block_threads, obs_split=self.obs_split, packed=self.packed)
+
+
+_lib = None
+_lock = threading.Lock()
+
+EXPORTS = [
+    "lsp_status_string", "lsp_last_error", "lsp_default_opts", "lsp_version", "lsp_workspace_size",
+    "lsp_periodogram", "lsp_batch", "lsp_argmax_period", "lsp_plan_create", "lsp_plan_execute",
+    "lsp_plan_execute_host", "lsp_plan_autotune", "lsp_plan_get_config", "lsp_plan_set_config",
+    "lsp_plan_destroy", "lsp_plan_enable_timing", "lsp_plan_main_kernel_ms", "lsp_plan_kernel_count",
+]
+
+
+def lib():
+    """The loaded CUDA library (raises LibraryNotBuilt if it was never built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise LibraryNotBuilt(
+                    f"{LIB_PATH} is missing: build it with `python -m paper_2105_04006_gb300.build` "
+                    "(or __graft_entry__.build()); there is no CPU fallback")
+            L = ctypes.CDLL(LIB_PATH)
+            P, i32, i64, sz = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_size_t
+            GP, OP = ctypes.POINTER(Grid), ctypes.POINTER(Opts)
+            L.lsp_status_string.argtypes = [i32]
+            L.lsp_status_string.restype = ctypes.c_char_p
+            L.lsp_last_error.restype = ctypes.c_char_p
+            L.lsp_default_opts.restype = Opts
+            L.lsp_version.restype = i32
+            L.lsp_workspace_size.argtypes = [i64, i64, GP, OP, ctypes.POINTER(sz)]
+            L.lsp_periodogram.argtypes = [P, P, i64, GP, OP, P, P, P, sz, P]
+            L.lsp_batch.argtypes = [P, P, P, i64, i64, GP, OP, P, P, P, sz, P]
+            L.lsp_argmax_period.argtypes = [P, i64, i64, GP, i32, P, P]
+            L.lsp_plan_create.argtypes = [ctypes.POINTER(P), i64, i64, GP, OP]
+            L.lsp_plan_execute.argtypes = [P, P, P, P, P, P, P]
+            L.lsp_plan_execute_host.argtypes = [P, P, P, P, P, P, P]
+            L.lsp_plan_autotune.argtypes = [P, P, P, P, ctypes.c_char_p, P]
+            L.lsp_plan_get_config.argtypes = [P, ctypes.POINTER(Config)]
+            L.lsp_plan_set_config.argtypes = [P, ctypes.POINTER(Config)]
+            L.lsp_plan_enable_timing.argtypes = [P, i32]
+            L.lsp_plan_main_kernel_ms.argtypes = [P, ctypes.POINTER(ctypes.c_float)]
+            L.lsp_plan_kernel_count.argtypes = [P, ctypes.POINTER(i32)]
+            L.lsp_plan_destroy.argtypes = [P]
+            L.lsp_plan_destroy.restype = None
+            for name in EXPORTS:
+                if name not in ("lsp_status_string", "lsp_last_error", "lsp_default_opts",
+                                "lsp_version", "lsp_plan_destroy"):
+                    getattr(L, name).restype = i32
+            _lib = L
+    return _lib
+
+
+def _check(status: int):
+    if status != 0:
+        msg = lib().lsp_last_error().decode()
+        raise LSPError(status, msg)
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream_handle(device):
+    torch = _torch()
+    return ctypes.c_void_p(torch.cuda.current_stream(device).cuda_stream)
+
+
+def _ptr(x):
+    return ctypes.c_void_p(0 if x is None else x.data_ptr())
+
+
+def _require(x, name, dtype, device=None):
+    torch = _torch()
+    if not isinstance(x, torch.Tensor):
+        raise TypeError(f"{name} must be a torch tensor")
+    if x.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {x.dtype}")
+    if not x.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if device is not None and x.device != device:
+        raise ValueError(f"{name} is on {x.device}, expected {device}")
+    if not x.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+
+
+def make_opts(precision="fp32", norm="standard", center=True, top_k=1, k_reseed=0,
+              freqs_per_thread=0, block_threads=0, obs_split=0) -> Opts:
+    prec = {"fp32": FP32, "fp64": FP64, FP32: FP32, FP64: FP64}[precision]
+    nrm = {"standard": NORM_STANDARD, "psd": NORM_PSD, NORM_PSD: NORM_PSD,
+           NORM_STANDARD: NORM_STANDARD}[norm]
+    return Opts(prec, nrm, int(bool(center)), int(top_k), int(k_reseed), int(freqs_per_thread),
+                int(block_threads), int(obs_split))
+
+
+def _dtypes(opts: Opts):
+    torch = _torch()
+    return torch.float64 if opts.precision == FP64 else torch.float32
+
+
+def workspace_size(n_obj, total_nt, grid: Grid, opts: Opts) -> int:
+    n = ctypes.c_size_t(0)
+    _check(lib().lsp_workspace_size(int(n_obj), int(total_nt), ctypes.byref(grid), ctypes.byref(opts),
+                                    ctypes.byref(n)))
+    return int(n.value)
+
+
+def peaks_to_numpy(peaks) -> np.ndarray:
+    """Copy a peaks buffer (uint8 tensor of 40-byte records) to a structured array."""
+    host = peaks.detach().to("cpu").numpy() if hasattr(peaks, "detach") else np.asarray(peaks)
+    return host.view(PEAK_DTYPE).reshape(-1)
+
+
+def periodogram(t, y, grid: Grid, *, return_power=True, workspace=None, **kw):
+    """Single-object periodogram on the GPU.
+
+    t: float64 CUDA tensor [n_t]; y: float32 (fp32) or float64 (fp64) [n_t].
+    Returns (power or None, peaks) with peaks a uint8 tensor of top_k records
+    (``peaks_to_numpy`` decodes them).
+    """
+    torch = _torch()
+    opts = make_opts(**kw)
+    _require(t, "t", torch.float64)
+    _require(y, "y", _dtypes(opts), t.device)
+    n_t = t.numel()
+    if y.numel() != n_t:
+        raise ValueError("t and y differ in length")
+    ws_bytes = workspace_size(1, n_t, grid, opts)
+    ws = workspace if workspace is not None else torch.empty(max(ws_bytes, 256), dtype=torch.uint8,
+                                                                device=t.device)
+    power = torch.empty(grid.n_f, dtype=_dtypes(opts), device=t.device) if return_power else None
+    peaks = torch.empty(opts.top_k * 40, dtype=torch.uint8, device=t.device)
+    _check(lib().lsp_periodogram(_ptr(t), _ptr(y), n_t, ctypes.byref(grid), ctypes.byref(opts),
+                                 _ptr(power), _ptr(peaks), _ptr(ws), ws.numel(), _stream_handle(t.device)))
+    return power, peaks
+
+
+def batch(t, y, offsets, grid: Grid, *, return_power=False, workspace=None, **kw):
+    """Ragged batch (CSR offsets, int64 CUDA tensor of n_obj + 1) on the GPU.
+
+    Returns (power [n_obj, n_f] or None, peaks uint8 tensor of n_obj*top_k records).
+    """
+    torch = _torch()
+    opts = make_opts(**kw)
+    _require(t, "t", torch.float64)
+    _require(y, "y", _dtypes(opts), t.device)
+    _require(offsets, "offsets", torch.int64, t.device)
+    n_obj = offsets.numel() - 1
+    total = t.numel()
+    ws_bytes = workspace_size(n_obj, total, grid, opts)
+    ws = workspace if workspace is not None else torch.empty(max(ws_bytes, 256), dtype=torch.uint8,
+                                                                device=t.device)
+    power = (torch.empty((n_obj, grid.n_f), dtype=_dtypes(opts), device=t.device)
+             if return_power else None)
+    peaks = torch.empty(max(n_obj, 0) * opts.top_k * 40, dtype=torch.uint8, device=t.device)
+    _check(lib().lsp_batch(_ptr(t), _ptr(y), _ptr(offsets), n_obj, total, ctypes.byref(grid),
+                           ctypes.byref(opts), _ptr(power), _ptr(peaks), _ptr(ws), ws.numel(),
+                           _stream_handle(t.device)))
+    return power, peaks
+
+
+def argmax_period(power, grid: Grid):
+    """First maximum of each row of a stored periodogram (float32 or float64 CUDA tensor)."""
+    torch = _torch()
+    if power.dtype not in (torch.float32, torch.float64):
+        raise TypeError("power must be float32 or float64")
+    _require(power, "power", power.dtype)
+    p2 = power.reshape(-1, grid.n_f)
+    n_obj = p2.shape[0]
+    peaks = torch.empty(n_obj * 40, dtype=torch.uint8, device=power.device)
+    prec = FP64 if power.dtype == torch.float64 else FP32
+    _check(lib().lsp_argmax_period(_ptr(p2), n_obj, grid.n_f, ctypes.byref(grid), prec, _ptr(peaks),
+                                   _stream_handle(power.device)))
+    return peaks
+
+
+class Plan:
+    """A tuned, graph-captured periodogram job for one shape (``lsp_plan_*``)."""
+
+    def __init__(self, n_obj: int, total_nt: int, grid: Grid, **kw):
+        self.opts = make_opts(**kw)
+        self.grid = grid
+        self.n_obj = int(n_obj)
+        self.total_nt = int(total_nt)
+        h = ctypes.c_void_p()
+        _check(lib().lsp_plan_create(ctypes.byref(h), self.n_obj, self.total_nt, ctypes.byref(grid),
+                                     ctypes.byref(self.opts)))
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().lsp_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def config(self) -> dict:
+        c = Config()
+        _check(lib().lsp_plan_get_config(self._h, ctypes.byref(c)))
+        return c.as_dict()
+
+    def set_config(self, **cfg):
+        c = Config()
+        _check(lib().lsp_plan_get_config(self._h, ctypes.byref(c)))
+        for k, v in cfg.items():
+            setattr(c, k, int(v))
+        _check(lib().lsp_plan_set_config(self._h, ctypes.byref(c)))
+
+    def enable_timing(self, on: bool = True):
+        """Record events around the main kernel of every execution (re-captures)."""
+        _check(lib().lsp_plan_enable_timing(self._h, int(bool(on))))
+
+    def main_kernel_ms(self) -> float:
+        """Main-kernel duration of the last execution (waits for it)."""
+        v = ctypes.c_float()
+        _check(lib().lsp_plan_main_kernel_ms(self._h, ctypes.byref(v)))
+        return float(v.value)
+
+    @property
+    def kernel_count(self) -> int:
+        v = ctypes.c_int32()
+        _check(lib().lsp_plan_kernel_count(self._h, ctypes.byref(v)))
+        return int(v.value)
+
+    def peaks_buffer(self, device):
+        torch = _torch()
+        return torch.empty(self.n_obj * self.opts.top_k * 40, dtype=torch.uint8, device=device)
+
+    def execute(self, t, y, offsets=None, power=None, peaks=None):
+        """Run on device tensors; returns the peaks tensor (allocated if not given)."""
+        torch = _torch()
+        _require(t, "t", torch.float64)
+        _require(y, "y", _dtypes(self.opts), t.device)
+        if offsets is not None:
+            _require(offsets, "offsets", torch.int64, t.device)
+        if peaks is None:
+            peaks = self.peaks_buffer(t.device)
+        _check(lib().lsp_plan_execute(self._h, _ptr(t), _ptr(y), _ptr(offsets), _ptr(power), _ptr(peaks),
+                                      _stream_handle(t.device)))
+        return peaks
+
+    def execute_host(self, t, y, offsets=None, power=None, peaks=None, device=None):
+        """End-to-end on host buffers (numpy arrays or CPU tensors, pinned is fastest).
+
+        Copies inputs in, runs, copies the peaks (and power if given) out, and
+        synchronises.  Returns the peaks as a structured numpy array.
+        """
+        torch = _torch()
+        dev = device or torch.device("cuda", torch.cuda.current_device())
+
+        def hptr(a, dtype):
+            if a is None:
+                return ctypes.c_void_p(0)
+            if isinstance(a, np.ndarray):
+                if a.dtype != dtype or not a.flags.c_contiguous:
+                    raise TypeError(f"host array must be contiguous {dtype}")
+                return ctypes.c_void_p(a.ctypes.data)
+            if a.is_cuda or not a.is_contiguous():
+                raise TypeError("host tensor must be a contiguous CPU tensor")
+            return ctypes.c_void_p(a.data_ptr())
+
+        ydt = np.float64 if self.opts.precision == FP64 else np.float32
+        if peaks is None:
+            peaks = np.empty(self.n_obj * self.opts.top_k, dtype=PEAK_DTYPE)
+        pk_ptr = (ctypes.c_void_p(peaks.ctypes.data) if isinstance(peaks, np.ndarray)
+                  else ctypes.c_void_p(peaks.data_ptr()))
+        _check(lib().lsp_plan_execute_host(self._h, hptr(t, np.float64), hptr(y, ydt),
+                                           hptr(offsets, np.int64), hptr(power, ydt), pk_ptr,
+                                           _stream_handle(dev)))
+        return peaks
+
+    def autotune(self, t, y, offsets=None, cache_path=None):
+        torch = _torch()
+        _require(t, "t", torch.float64)
+        _require(y, "y", _dtypes(self.opts), t.device)
+        cp = cache_path.encode() if cache_path else None
+        _check(lib().lsp_plan_autotune(self._h, _ptr(t), _ptr(y), _ptr(offsets), cp,
+                                       _stream_handle(t.device)))
+        return self.config

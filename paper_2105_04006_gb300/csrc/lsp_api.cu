@@ -1,0 +1,814 @@
+// lsp_api.cu -- the C ABI of include/lsp.h: validation, workspace layout,
+// launch sequence, plans (CUDA-graph replay, host entry point, autotuner).
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <fstream>
+#include <mutex>
+#include <sstream>
+#include <string>
+#include <vector>
+
+#include "../../include/lsp.h"
+#include "lsp_launch.h"
+
+using namespace lsp;
+
+static_assert(sizeof(lsp_peak) == 40, "lsp_peak layout");
+static_assert(sizeof(RecF32) == 32 && sizeof(RecF64) == 48, "record layout");
+
+namespace {
+
+thread_local std::string g_err;
+
+lsp_status fail(lsp_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return s;
+}
+
+lsp_status cuda_fail(cudaError_t e, const char* what) {
+  return fail(LSP_E_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define LSP_CUDA(call, what)                       \
+  do {                                             \
+    cudaError_t e__ = (call);                      \
+    if (e__ != cudaSuccess) return cuda_fail(e__, what); \
+  } while (0)
+
+constexpr size_t kAlign = 256;
+size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+int current_sm_count() {
+  static std::mutex mu;
+  static int cache[64] = {0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 152;
+  std::lock_guard<std::mutex> lk(mu);
+  if (cache[dev] == 0) {
+    int n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) {
+      cudaGetLastError();
+      n = 152;
+    }
+    cache[dev] = n;
+  }
+  return cache[dev];
+}
+
+// Resolved configuration and workspace layout of one call.
+struct Layout {
+  int prec, packed, k, fpt, threads, split, top_k, top, norm, center;
+  int64_t n_obj, total_nt, n_f;
+  double f_min, df;
+  int32_t n_chunks, n_res_chunks;
+  int64_t n_items;
+  int grid;  // persistent CTAs
+  size_t off_obj, off_rec, off_order, off_hist, off_queue, off_best, off_cand, off_part, total;
+};
+
+constexpr int64_t kMaxNf = (int64_t)1 << 31;  // k0 + F must fit in 32 bits
+constexpr int kMinObsPerSplit = 32;
+constexpr int kMaxObsPerSplit = 8192;  // bounds each FP32 partial sum
+constexpr int kMaxSplit = 256;
+
+lsp_status check_grid(const lsp_grid* g) {
+  if (!g) return fail(LSP_E_ARG, "grid is NULL");
+  if (!std::isfinite(g->f_min) || !std::isfinite(g->f_max))
+    return fail(LSP_E_ARG, "grid limits must be finite");
+  if (!(g->f_min > 0.0)) return fail(LSP_E_ARG, "f_min must be > 0 (Eq. 1 divides by 2w)");
+  if (!(g->f_max > g->f_min)) return fail(LSP_E_ARG, "f_max must be > f_min");
+  if (g->n_f < 1 || g->n_f > kMaxNf - 65536) return fail(LSP_E_ARG, "n_f must be in [1, 2^31 - 2^16]");
+  return LSP_OK;
+}
+
+lsp_status resolve(int64_t n_obj, int64_t total_nt, const lsp_grid* g, const lsp_opts* opts_in,
+                   const lsp_config* cfg, Layout* L) {
+  lsp_status st = check_grid(g);
+  if (st) return st;
+  if (n_obj < 0 || n_obj > INT32_MAX) return fail(LSP_E_ARG, "n_obj out of range");
+  if (total_nt < 0) return fail(LSP_E_ARG, "total_nt must be >= 0");
+  if (n_obj == 1 && total_nt > INT32_MAX) return fail(LSP_E_ARG, "n_t must be < 2^31");
+  lsp_opts o = opts_in ? *opts_in : lsp_default_opts();
+  if (o.precision != LSP_FP32 && o.precision != LSP_FP64) return fail(LSP_E_ARG, "bad precision");
+  if (o.norm != LSP_NORM_PSD && o.norm != LSP_NORM_STANDARD) return fail(LSP_E_ARG, "bad norm");
+  if (o.top_k < 1 || o.top_k > 3) return fail(LSP_E_ARG, "top_k must be 1..3");
+  if (o.k_reseed < 0 || o.freqs_per_thread < 0 || o.block_threads < 0 || o.obs_split < 0)
+    return fail(LSP_E_ARG, "negative option");
+
+  Layout& l = *L;
+  memset(&l, 0, sizeof l);
+  l.prec = o.precision;
+  l.norm = o.norm;
+  l.center = o.center_y ? 1 : 0;
+  l.top_k = o.top_k;
+  l.top = o.top_k > 1;
+  l.n_obj = n_obj;
+  l.total_nt = total_nt;
+  l.n_f = g->n_f;
+  l.f_min = g->f_min;
+  l.df = (g->f_max - g->f_min) / (double)g->n_f;
+
+  int k, fpt, threads, packed, split_req;
+  if (cfg) {
+    k = cfg->k_reseed;
+    fpt = cfg->freqs_per_thread;
+    threads = cfg->block_threads;
+    packed = cfg->packed;
+    split_req = cfg->obs_split;
+  } else {
+    k = o.k_reseed ? o.k_reseed : 8;
+    if (l.prec == LSP_FP64) {
+      fpt = o.freqs_per_thread ? o.freqs_per_thread : k;
+      threads = o.block_threads ? o.block_threads : 128;
+    } else {
+      fpt = o.freqs_per_thread ? o.freqs_per_thread
+                               : (main_variant_exists(0, 1, k, 2 * k) ? 2 * k : k);
+      threads = o.block_threads ? o.block_threads : 256;
+    }
+    packed = (l.prec == LSP_FP32 && fpt == 2 * k) ? 1 : 0;
+    split_req = o.obs_split;
+  }
+  if (threads < 64 || threads > 256 || threads % 32)
+    return fail(LSP_E_ARG, "block_threads must be a multiple of 32 in [64, 256]");
+  if (!main_variant_exists(l.prec, packed, k, fpt))
+    return fail(LSP_E_UNSUPPORTED, "no kernel for precision %d with k_reseed=%d, freqs_per_thread=%d",
+                l.prec, k, fpt);
+  l.k = k;
+  l.fpt = fpt;
+  l.threads = threads;
+  l.packed = packed;
+
+  const int64_t chunk = (int64_t)threads * fpt;
+  l.n_chunks = (int32_t)((l.n_f + chunk - 1) / chunk);
+  int split = 1;
+  if (n_obj == 1) {
+    if (split_req > 0) {
+      split = split_req;
+    } else {
+      const int64_t target = (int64_t)current_sm_count() * 4;
+      int64_t s = (target + l.n_chunks - 1) / l.n_chunks;
+      int64_t s_min = (total_nt + kMaxObsPerSplit - 1) / kMaxObsPerSplit;
+      if (s < s_min) s = s_min;
+      int64_t s_max = total_nt / kMinObsPerSplit;
+      if (s > s_max) s = s_max;
+      split = (int)(s < 1 ? 1 : s);
+    }
+    if (split > kMaxSplit) split = kMaxSplit;
+  }
+  l.split = split;
+  const int64_t cchunk = (int64_t)kCombineThreads * kCombinePerThread;
+  l.n_res_chunks = split > 1 ? (int32_t)((l.n_f + cchunk - 1) / cchunk) : l.n_chunks;
+  l.n_items = n_obj * (int64_t)l.n_chunks * split;
+
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    size_t at = off;
+    off = align_up(off + bytes);
+    return at;
+  };
+  l.off_obj = take((size_t)n_obj * sizeof(ObjInfo));
+  l.off_rec = take((size_t)total_nt * (l.prec ? sizeof(RecF64) : sizeof(RecF32)));
+  l.off_order = take(n_obj > 1 ? (size_t)n_obj * sizeof(int32_t) : 0);
+  l.off_hist = take(n_obj > 1 ? (LSP_HIST_BINS + 1) * sizeof(uint32_t) : 0);
+  l.off_queue = take(16);
+  l.off_best = take((size_t)n_obj * l.n_res_chunks * sizeof(ChunkBest));
+  l.off_cand = take(l.top ? (size_t)n_obj * l.n_res_chunks * sizeof(ChunkCand) : 0);
+  l.off_part = take(split > 1 ? (size_t)split * l.n_f * 4 * (l.prec ? 8 : 4) : 0);
+  l.total = off;
+
+  int bps = main_blocks_per_sm(l.prec, l.packed, l.k, l.fpt, l.threads, l.top);
+  if (bps <= 0) {
+    cudaGetLastError();
+    bps = 1;
+  }
+  int64_t grid = (int64_t)bps * current_sm_count();
+  if (grid > l.n_items) grid = l.n_items;
+  l.grid = (int)(grid < 1 ? 1 : grid);
+  return LSP_OK;
+}
+
+// The launch sequence of one periodogram call (stream-ordered, no syncs).
+lsp_status run(const Layout& L, const double* t, const void* y, const int64_t* offsets,
+               void* power_out, lsp_peak* peaks, char* ws, cudaStream_t st,
+               cudaEvent_t ev_main0 = nullptr, cudaEvent_t ev_main1 = nullptr) {
+  if (L.n_obj == 0) return LSP_OK;
+  ObjInfo* obj = (ObjInfo*)(ws + L.off_obj);
+  void* rec = ws + L.off_rec;
+  int32_t* order = L.n_obj > 1 ? (int32_t*)(ws + L.off_order) : nullptr;
+  uint32_t* hist = (uint32_t*)(ws + L.off_hist);
+  uint32_t* queue = (uint32_t*)(ws + L.off_queue);
+  ChunkBest* best = (ChunkBest*)(ws + L.off_best);
+  ChunkCand* cand = L.top ? (ChunkCand*)(ws + L.off_cand) : nullptr;
+  void* part = L.split > 1 ? (void*)(ws + L.off_part) : nullptr;
+  const bool y64 = L.prec == LSP_FP64;
+
+  LSP_CUDA(launch_stats(t, y, y64, offsets, L.n_obj, L.total_nt, L.center,
+                        L.norm, obj, st),
+           "prologue (statistics)");
+  LSP_CUDA(launch_records(t, y, y64, obj, L.n_obj, L.total_nt, L.f_min, L.df, y64, rec, st),
+           "prologue (records)");
+  if (order) LSP_CUDA(launch_lpt_order(obj, L.n_obj, hist, order, st), "work-queue order");
+  LSP_CUDA(cudaMemsetAsync(queue, 0, 16, st), "queue reset");
+  MainLaunch ml;
+  ml.prec = L.prec;
+  ml.packed = L.packed;
+  ml.k_reseed = L.k;
+  ml.fpt = L.fpt;
+  ml.threads = L.threads;
+  ml.grid = L.grid;
+  ml.top = L.top && L.split == 1;
+  ml.rec = rec;
+  ml.obj = obj;
+  ml.order = order;
+  ml.power_out = L.split == 1 ? power_out : nullptr;
+  ml.part = part;
+  ml.best = best;
+  ml.cand = L.split == 1 ? cand : nullptr;
+  ml.queue = queue;
+  ml.n_f = L.n_f;
+  ml.n_chunks = L.n_chunks;
+  ml.split = L.split;
+  ml.n_items = L.n_items;
+  if (ev_main0) LSP_CUDA(cudaEventRecord(ev_main0, st), "timing event");
+  LSP_CUDA(launch_main(ml, st), "main kernel");
+  if (ev_main1) LSP_CUDA(cudaEventRecord(ev_main1, st), "timing event");
+  if (L.split > 1)
+    LSP_CUDA(launch_combine(L.prec, part, L.split, L.n_f, obj, power_out, best, cand, st),
+             "split combine");
+  if (peaks)
+    LSP_CUDA(launch_finalize(obj, best, cand, L.n_obj, L.n_res_chunks, L.top_k, L.f_min, L.df,
+                             peaks, st),
+             "finalize");
+  return LSP_OK;
+}
+
+lsp_status check_ws(const Layout& L, void* ws, size_t ws_bytes) {
+  if (L.total && !ws) return fail(LSP_E_WORKSPACE, "workspace is NULL (need %zu bytes)", L.total);
+  if (ws_bytes < L.total)
+    return fail(LSP_E_WORKSPACE, "workspace has %zu bytes, need %zu", ws_bytes, L.total);
+  if (((uintptr_t)ws) % kAlign) return fail(LSP_E_WORKSPACE, "workspace must be 256-byte aligned");
+  return LSP_OK;
+}
+
+lsp_status check_io(int64_t n, const double* t, const void* y) {
+  if (n > 0 && (!t || !y)) return fail(LSP_E_ARG, "t and y must not be NULL");
+  return LSP_OK;
+}
+
+}  // namespace
+
+// ======================================================================= C ABI
+extern "C" {
+
+const char* lsp_status_string(lsp_status s) {
+  switch (s) {
+    case LSP_OK: return "LSP_OK";
+    case LSP_E_ARG: return "LSP_E_ARG: invalid argument";
+    case LSP_E_CUDA: return "LSP_E_CUDA: CUDA runtime error";
+    case LSP_E_NOMEM: return "LSP_E_NOMEM: device allocation failed";
+    case LSP_E_WORKSPACE: return "LSP_E_WORKSPACE: workspace too small or misaligned";
+    case LSP_E_NUMERIC: return "LSP_E_NUMERIC: numeric problem";
+    case LSP_E_TIMEOUT: return "LSP_E_TIMEOUT: device wait timed out";
+    case LSP_E_UNSUPPORTED: return "LSP_E_UNSUPPORTED: not implemented in this build";
+  }
+  return "unknown lsp_status";
+}
+
+const char* lsp_last_error(void) { return g_err.c_str(); }
+
+int32_t lsp_version(void) { return 10000; }
+
+lsp_opts lsp_default_opts(void) {
+  lsp_opts o;
+  memset(&o, 0, sizeof o);
+  o.precision = LSP_FP32;
+  o.norm = LSP_NORM_STANDARD;
+  o.center_y = 1;
+  o.top_k = 1;
+  return o;
+}
+
+lsp_status lsp_workspace_size(int64_t n_obj, int64_t total_nt, const lsp_grid* grid,
+                              const lsp_opts* opts, size_t* bytes) {
+  if (!bytes) return fail(LSP_E_ARG, "bytes is NULL");
+  Layout L;
+  lsp_status st = resolve(n_obj, total_nt, grid, opts, nullptr, &L);
+  if (st) return st;
+  *bytes = L.total;
+  return LSP_OK;
+}
+
+lsp_status lsp_periodogram(const double* t, const void* y, int64_t n_t, const lsp_grid* grid,
+                           const lsp_opts* opts, void* power_out, lsp_peak* peaks, void* workspace,
+                           size_t ws_bytes, lsp_stream_t stream) {
+  g_err.clear();
+  Layout L;
+  lsp_status st = resolve(1, n_t, grid, opts, nullptr, &L);
+  if (st) return st;
+  if ((st = check_io(n_t, t, y))) return st;
+  if ((st = check_ws(L, workspace, ws_bytes))) return st;
+  return run(L, t, y, nullptr, power_out, peaks, (char*)workspace, (cudaStream_t)stream);
+}
+
+lsp_status lsp_batch(const double* t, const void* y, const int64_t* offsets, int64_t n_obj,
+                     int64_t total_nt, const lsp_grid* grid, const lsp_opts* opts, void* power_out,
+                     lsp_peak* peaks, void* workspace, size_t ws_bytes, lsp_stream_t stream) {
+  g_err.clear();
+  Layout L;
+  lsp_status st = resolve(n_obj, total_nt, grid, opts, nullptr, &L);
+  if (st) return st;
+  if (n_obj == 0) return LSP_OK;
+  if (!offsets) return fail(LSP_E_ARG, "offsets must not be NULL");
+  if ((st = check_io(total_nt, t, y))) return st;
+  if ((st = check_ws(L, workspace, ws_bytes))) return st;
+  return run(L, t, y, offsets, power_out, peaks, (char*)workspace, (cudaStream_t)stream);
+}
+
+lsp_status lsp_argmax_period(const void* power, int64_t n_obj, int64_t n_f, const lsp_grid* grid,
+                             int32_t precision, lsp_peak* peaks, lsp_stream_t stream) {
+  g_err.clear();
+  lsp_status st = check_grid(grid);
+  if (st) return st;
+  if (n_f != grid->n_f) return fail(LSP_E_ARG, "n_f must equal grid->n_f");
+  if (n_obj < 0) return fail(LSP_E_ARG, "n_obj must be >= 0");
+  if (precision != LSP_FP32 && precision != LSP_FP64) return fail(LSP_E_ARG, "bad precision");
+  if (n_obj == 0) return LSP_OK;
+  if (!power || !peaks) return fail(LSP_E_ARG, "power and peaks must not be NULL");
+  if (((uintptr_t)peaks) % 8) return fail(LSP_E_ARG, "peaks must be 8-byte aligned");
+  const double df = (grid->f_max - grid->f_min) / (double)grid->n_f;
+  LSP_CUDA(launch_argmax_period(power, precision == LSP_FP64, n_obj, n_f, grid->f_min, df, peaks,
+                                (cudaStream_t)stream),
+           "argmax");
+  return LSP_OK;
+}
+
+}  // extern "C"
+
+// ======================================================================= plans
+struct lsp_plan {
+  Layout L;
+  lsp_grid grid;
+  lsp_opts opts;
+  lsp_config cfg;
+  int64_t n_obj = 0, total_nt = 0;
+  int device = 0;
+  char* ws = nullptr;
+  size_t ws_cap = 0;
+  cudaStream_t cap_stream = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  const void* cap_args[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;  // timing probe (nullptr: off)
+  // staging of the host entry point (allocated by its first call)
+  double* d_t = nullptr;
+  void* d_y = nullptr;
+  int64_t* d_off = nullptr;
+  lsp_peak* d_peaks = nullptr;
+  void* d_power = nullptr;
+};
+
+namespace {
+
+lsp_config config_of(const Layout& L) {
+  lsp_config c;
+  memset(&c, 0, sizeof c);
+  c.k_reseed = L.k;
+  c.freqs_per_thread = L.fpt;
+  c.block_threads = L.threads;
+  c.obs_split = L.split;
+  c.packed = L.packed;
+  return c;
+}
+
+void drop_graph(lsp_plan* p) {
+  if (p->exec) cudaGraphExecDestroy(p->exec);
+  if (p->graph) cudaGraphDestroy(p->graph);
+  p->exec = nullptr;
+  p->graph = nullptr;
+  for (auto& a : p->cap_args) a = nullptr;
+}
+
+lsp_status ensure_ws(lsp_plan* p, size_t bytes) {
+  if (bytes <= p->ws_cap) return LSP_OK;
+  drop_graph(p);  // a captured graph may reference the old workspace
+  if (p->ws) {
+    cudaDeviceSynchronize();
+    cudaFree(p->ws);
+  }
+  p->ws = nullptr;
+  p->ws_cap = 0;
+  if (cudaMalloc(&p->ws, bytes ? bytes : kAlign) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(LSP_E_NOMEM, "plan workspace of %zu bytes", bytes);
+  }
+  p->ws_cap = bytes;
+  return LSP_OK;
+}
+
+lsp_status apply_config(lsp_plan* p, const lsp_config* c) {
+  Layout L;
+  lsp_status st = resolve(p->n_obj, p->total_nt, &p->grid, &p->opts, c, &L);
+  if (st) return st;
+  if ((st = ensure_ws(p, L.total))) return st;
+  p->L = L;
+  p->cfg = config_of(L);
+  drop_graph(p);
+  return LSP_OK;
+}
+
+// Times `reps` runs of the plan's current layout with events on `st`.
+lsp_status time_runs(lsp_plan* p, const double* t, const void* y, const int64_t* off, int reps,
+                     cudaStream_t st, float* ms) {
+  cudaEvent_t a, b;
+  LSP_CUDA(cudaEventCreate(&a), "event");
+  LSP_CUDA(cudaEventCreate(&b), "event");
+  lsp_status s = run(p->L, t, y, off, nullptr, nullptr, p->ws, st);  // warm-up
+  if (!s) {
+    cudaEventRecord(a, st);
+    for (int i = 0; i < reps && !s; ++i) s = run(p->L, t, y, off, nullptr, nullptr, p->ws, st);
+    cudaEventRecord(b, st);
+    cudaError_t e = cudaEventSynchronize(b);
+    if (e != cudaSuccess) s = cuda_fail(e, "autotune timing");
+    else cudaEventElapsedTime(ms, a, b);
+    *ms /= reps;
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  return s;
+}
+
+std::string tune_key(const lsp_plan* p) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceProp prop;
+  memset(&prop, 0, sizeof prop);
+  cudaGetDeviceProperties(&prop, dev);
+  auto cls = [](int64_t x) { int c = 0; while (x > 1) { x >>= 1; ++c; } return c; };
+  char buf[512];
+  snprintf(buf, sizeof buf, "%s|sm%d|p%d|n%d|k%d|obj%d|nt%d|nf%d", prop.name,
+           prop.multiProcessorCount, p->opts.precision, p->opts.norm, p->opts.top_k,
+           cls(p->n_obj), cls(p->n_obj ? p->total_nt / p->n_obj : 0), cls(p->grid.n_f));
+  return buf;
+}
+
+bool cache_lookup(const char* path, const std::string& key, lsp_config* c) {
+  std::ifstream f(path);
+  if (!f) return false;
+  std::string line;
+  bool found = false;
+  const std::string needle = "\"key\": \"" + key + "\"";
+  while (std::getline(f, line)) {
+    if (line.find(needle) == std::string::npos) continue;
+    lsp_config t;
+    memset(&t, 0, sizeof t);
+    auto get = [&](const char* name, int32_t* v) {
+      std::string k = std::string("\"") + name + "\": ";
+      size_t at = line.find(k);
+      if (at == std::string::npos) return false;
+      return sscanf(line.c_str() + at + k.size(), "%d", v) == 1;
+    };
+    if (get("k_reseed", &t.k_reseed) && get("freqs_per_thread", &t.freqs_per_thread) &&
+        get("block_threads", &t.block_threads) && get("obs_split", &t.obs_split) &&
+        get("packed", &t.packed)) {
+      *c = t;
+      found = true;
+    }
+  }
+  return found;
+}
+
+void cache_store(const char* path, const std::string& key, const lsp_config& c, float ms, double err) {
+  std::ofstream f(path, std::ios::app);
+  if (!f) return;
+  f << "{\"key\": \"" << key << "\", \"k_reseed\": " << c.k_reseed << ", \"freqs_per_thread\": "
+    << c.freqs_per_thread << ", \"block_threads\": " << c.block_threads << ", \"obs_split\": "
+    << c.obs_split << ", \"packed\": " << c.packed << ", \"ms\": " << ms << ", \"max_err\": " << err
+    << "}\n";
+}
+
+}  // namespace
+
+extern "C" {
+
+lsp_status lsp_plan_create(lsp_plan** plan, int64_t n_obj, int64_t total_nt, const lsp_grid* grid,
+                           const lsp_opts* opts) {
+  g_err.clear();
+  if (!plan) return fail(LSP_E_ARG, "plan is NULL");
+  *plan = nullptr;
+  if (n_obj < 1) return fail(LSP_E_ARG, "a plan needs n_obj >= 1");
+  Layout L;
+  lsp_status st = resolve(n_obj, total_nt, grid, opts, nullptr, &L);
+  if (st) return st;
+  lsp_plan* p = new lsp_plan();
+  p->L = L;
+  p->grid = *grid;
+  p->opts = opts ? *opts : lsp_default_opts();
+  p->cfg = config_of(L);
+  p->n_obj = n_obj;
+  p->total_nt = total_nt;
+  cudaGetDevice(&p->device);
+  if ((st = ensure_ws(p, L.total))) {
+    delete p;
+    return st;
+  }
+  if (cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    lsp_plan_destroy(p);
+    return fail(LSP_E_CUDA, "plan stream");
+  }
+  *plan = p;
+  return LSP_OK;
+}
+
+void lsp_plan_destroy(lsp_plan* p) {
+  if (!p) return;
+  drop_graph(p);
+  if (p->ev0) cudaEventDestroy(p->ev0);
+  if (p->ev1) cudaEventDestroy(p->ev1);
+  if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
+  cudaFree(p->ws);
+  cudaFree(p->d_t);
+  cudaFree(p->d_y);
+  cudaFree(p->d_off);
+  cudaFree(p->d_peaks);
+  cudaFree(p->d_power);
+  delete p;
+}
+
+lsp_status lsp_plan_enable_timing(lsp_plan* p, int32_t enable) {
+  g_err.clear();
+  if (!p) return fail(LSP_E_ARG, "plan is NULL");
+  drop_graph(p);
+  if (p->ev0) cudaEventDestroy(p->ev0);
+  if (p->ev1) cudaEventDestroy(p->ev1);
+  p->ev0 = p->ev1 = nullptr;
+  if (enable) {
+    LSP_CUDA(cudaEventCreate(&p->ev0), "timing event");
+    LSP_CUDA(cudaEventCreate(&p->ev1), "timing event");
+  }
+  return LSP_OK;
+}
+
+lsp_status lsp_plan_main_kernel_ms(lsp_plan* p, float* ms) {
+  g_err.clear();
+  if (!p || !ms) return fail(LSP_E_ARG, "NULL argument");
+  if (!p->ev0) return fail(LSP_E_ARG, "timing is not enabled on this plan");
+  LSP_CUDA(cudaEventSynchronize(p->ev1), "timing event");
+  LSP_CUDA(cudaEventElapsedTime(ms, p->ev0, p->ev1), "timing event");
+  return LSP_OK;
+}
+
+lsp_status lsp_plan_kernel_count(const lsp_plan* p, int32_t* count) {
+  if (!p || !count) return fail(LSP_E_ARG, "NULL argument");
+  const Layout& L = p->L;
+  // statistics + records + main (+ 3 for the LPT order) (+ combine) (+ finalize)
+  *count = 3 + (L.n_obj > 1 ? 3 : 0) + (L.split > 1 ? 1 : 0) + 1;
+  return LSP_OK;
+}
+
+lsp_status lsp_plan_get_config(const lsp_plan* p, lsp_config* c) {
+  if (!p || !c) return fail(LSP_E_ARG, "NULL argument");
+  *c = p->cfg;
+  return LSP_OK;
+}
+
+lsp_status lsp_plan_set_config(lsp_plan* p, const lsp_config* c) {
+  g_err.clear();
+  if (!p || !c) return fail(LSP_E_ARG, "NULL argument");
+  return apply_config(p, c);
+}
+
+lsp_status lsp_plan_execute(lsp_plan* p, const double* t, const void* y, const int64_t* offsets,
+                            void* power_out, lsp_peak* peaks, lsp_stream_t stream) {
+  g_err.clear();
+  if (!p) return fail(LSP_E_ARG, "plan is NULL");
+  lsp_status st = check_io(p->total_nt, t, y);
+  if (st) return st;
+  if (p->n_obj > 1 && !offsets) return fail(LSP_E_ARG, "offsets must not be NULL");
+  const void* args[5] = {t, y, offsets, power_out, peaks};
+  bool same = p->exec != nullptr;
+  for (int i = 0; i < 5 && same; ++i) same = args[i] == p->cap_args[i];
+  if (!same) {
+    drop_graph(p);
+    LSP_CUDA(cudaStreamBeginCapture(p->cap_stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+    st = run(p->L, t, y, offsets, power_out, peaks, p->ws, p->cap_stream, p->ev0, p->ev1);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(p->cap_stream, &g);
+    if (st) {
+      if (g) cudaGraphDestroy(g);
+      return st;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "end capture");
+    p->graph = g;
+    e = cudaGraphInstantiate(&p->exec, g, 0);
+    if (e != cudaSuccess) {
+      drop_graph(p);
+      return cuda_fail(e, "graph instantiate");
+    }
+    for (int i = 0; i < 5; ++i) p->cap_args[i] = args[i];
+  }
+  LSP_CUDA(cudaGraphLaunch(p->exec, (cudaStream_t)stream), "graph launch");
+  return LSP_OK;
+}
+
+lsp_status lsp_plan_execute_host(lsp_plan* p, const double* t, const void* y,
+                                 const int64_t* offsets, void* power_out, lsp_peak* peaks,
+                                 lsp_stream_t stream) {
+  g_err.clear();
+  if (!p) return fail(LSP_E_ARG, "plan is NULL");
+  lsp_status st = check_io(p->total_nt, t, y);
+  if (st) return st;
+  if (p->n_obj > 1 && !offsets) return fail(LSP_E_ARG, "offsets must not be NULL");
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t ysz = p->opts.precision == LSP_FP64 ? 8 : 4;
+  const size_t n_peaks = (size_t)p->n_obj * p->opts.top_k;
+  const size_t pbytes = (size_t)p->n_obj * p->grid.n_f * ysz;
+  auto alloc = [&](void** ptr, size_t bytes) -> lsp_status {
+    if (*ptr) return LSP_OK;
+    if (cudaMalloc(ptr, bytes ? bytes : 16) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(LSP_E_NOMEM, "staging buffer of %zu bytes", bytes);
+    }
+    return LSP_OK;
+  };
+  if ((st = alloc((void**)&p->d_t, p->total_nt * sizeof(double)))) return st;
+  if ((st = alloc(&p->d_y, p->total_nt * ysz))) return st;
+  if ((st = alloc((void**)&p->d_off, (p->n_obj + 1) * sizeof(int64_t)))) return st;
+  if ((st = alloc((void**)&p->d_peaks, n_peaks * sizeof(lsp_peak)))) return st;
+  if (power_out && (st = alloc(&p->d_power, pbytes))) return st;
+  LSP_CUDA(cudaMemcpyAsync(p->d_t, t, p->total_nt * sizeof(double), cudaMemcpyHostToDevice, s), "H2D t");
+  LSP_CUDA(cudaMemcpyAsync(p->d_y, y, p->total_nt * ysz, cudaMemcpyHostToDevice, s), "H2D y");
+  const int64_t* d_off = nullptr;
+  if (offsets) {
+    LSP_CUDA(cudaMemcpyAsync(p->d_off, offsets, (p->n_obj + 1) * sizeof(int64_t),
+                             cudaMemcpyHostToDevice, s), "H2D offsets");
+    d_off = p->d_off;
+  }
+  st = lsp_plan_execute(p, p->d_t, p->d_y, d_off, power_out ? p->d_power : nullptr,
+                        peaks ? p->d_peaks : nullptr, stream);
+  if (st) return st;
+  if (peaks)
+    LSP_CUDA(cudaMemcpyAsync(peaks, p->d_peaks, n_peaks * sizeof(lsp_peak), cudaMemcpyDeviceToHost, s),
+             "D2H peaks");
+  if (power_out)
+    LSP_CUDA(cudaMemcpyAsync(power_out, p->d_power, pbytes, cudaMemcpyDeviceToHost, s), "D2H power");
+  LSP_CUDA(cudaStreamSynchronize(s), "synchronize");
+  return LSP_OK;
+}
+
+lsp_status lsp_plan_autotune(lsp_plan* p, const double* t, const void* y, const int64_t* offsets,
+                             const char* cache_path, lsp_stream_t stream) {
+  g_err.clear();
+  if (!p) return fail(LSP_E_ARG, "plan is NULL");
+  lsp_status st = check_io(p->total_nt, t, y);
+  if (st) return st;
+  if (p->n_obj > 1 && !offsets) return fail(LSP_E_ARG, "offsets must not be NULL");
+  cudaStream_t s = (cudaStream_t)stream;
+  const std::string key = tune_key(p);
+  lsp_config cached;
+  if (cache_path && cache_lookup(cache_path, key, &cached)) {
+    if (!apply_config(p, &cached)) return LSP_OK;
+    g_err.clear();  // stale entry: tune again
+  }
+
+  // Candidates: reseed interval K, frequencies per thread, CTA size and (one
+  // object) the N_t split.
+  std::vector<lsp_config> cands;
+  auto add = [&](int k, int fpt, int thr, int packed, int split) {
+    lsp_config c;
+    memset(&c, 0, sizeof c);
+    c.k_reseed = k;
+    c.freqs_per_thread = fpt;
+    c.block_threads = thr;
+    c.packed = packed;
+    c.obs_split = split;
+    if (main_variant_exists(p->opts.precision, packed, k, fpt)) cands.push_back(c);
+  };
+  std::vector<int> splits = {0};
+  if (p->n_obj == 1) {
+    Layout L0;
+    if ((st = resolve(1, p->total_nt, &p->grid, &p->opts, nullptr, &L0))) return st;
+    for (int f : {2, 4}) {
+      if (L0.split * f <= kMaxSplit && p->total_nt / (L0.split * f) >= kMinObsPerSplit)
+        splits.push_back(L0.split * f);
+      if (L0.split / f >= 1) splits.push_back(L0.split / f);
+    }
+  }
+  for (int sp : splits) {
+    if (p->opts.precision == LSP_FP64) {
+      for (int k : {4, 8, 16})
+        for (int thr : {128, 256}) add(k, k, thr, 0, sp);
+    } else {
+      for (int k : {4, 8, 16})
+        for (int thr : {128, 256}) add(k, 2 * k, thr, 1, sp);
+      for (int k : {8, 16}) add(k, k, 256, 0, sp);
+    }
+  }
+
+  // Error gate (FP32): the first object's periodogram against the FP64 path.
+  int64_t g_lo = 0, g_n = p->total_nt;
+  if (p->n_obj > 1) {
+    int64_t h[2];
+    LSP_CUDA(cudaMemcpyAsync(h, offsets, sizeof h, cudaMemcpyDeviceToHost, s), "offsets probe");
+    LSP_CUDA(cudaStreamSynchronize(s), "offsets probe");
+    g_lo = h[0];
+    g_n = h[1] - h[0];
+  }
+  const bool gate = p->opts.precision == LSP_FP32 && g_n >= 2;
+  double* ref = nullptr;   // FP64 periodogram of the probe object
+  double* y64 = nullptr;
+  float* pw = nullptr;
+  double* d_err = nullptr;
+  char* gws = nullptr;
+  size_t gws_bytes = 0;
+  lsp_opts o64 = p->opts;
+  o64.precision = LSP_FP64;
+  o64.k_reseed = o64.freqs_per_thread = o64.block_threads = o64.obs_split = 0;
+  o64.top_k = 1;
+  o64.norm = LSP_NORM_STANDARD;  // the gate compares P_n (1e-4 absolute)
+  auto cleanup = [&]() {
+    cudaFree(ref);
+    cudaFree(y64);
+    cudaFree(pw);
+    cudaFree(d_err);
+    cudaFree(gws);
+  };
+  if (gate) {
+    Layout L64;
+    if ((st = resolve(1, g_n, &p->grid, &o64, nullptr, &L64))) return st;
+    gws_bytes = L64.total;
+    {  // room for every candidate's single-object layout too
+      for (const auto& c : cands) {
+        Layout Lc;
+        lsp_config c1 = c;
+        c1.obs_split = 1;
+        lsp_opts o1 = p->opts;
+        o1.top_k = 1;
+        o1.norm = LSP_NORM_STANDARD;
+        if (!resolve(1, g_n, &p->grid, &o1, &c1, &Lc) && Lc.total > gws_bytes) gws_bytes = Lc.total;
+      }
+    }
+    if (cudaMalloc(&ref, p->grid.n_f * sizeof(double)) || cudaMalloc(&y64, g_n * sizeof(double)) ||
+        cudaMalloc(&pw, p->grid.n_f * sizeof(float)) || cudaMalloc(&d_err, sizeof(double)) ||
+        cudaMalloc(&gws, gws_bytes)) {
+      cudaGetLastError();
+      cleanup();
+      return fail(LSP_E_NOMEM, "autotune scratch");
+    }
+    cudaError_t e = launch_f32_to_f64((const float*)y + g_lo, y64, g_n, s);
+    if (e != cudaSuccess) { cleanup(); return cuda_fail(e, "autotune convert"); }
+    if ((st = run(L64, t + g_lo, y64, nullptr, ref, nullptr, gws, s))) { cleanup(); return st; }
+  }
+
+  float best_ms = 1e30f;
+  double best_err = 0.0;
+  lsp_config best = p->cfg;
+  bool any = false;
+  for (const auto& c : cands) {
+    Layout Lc;
+    if (resolve(p->n_obj, p->total_nt, &p->grid, &p->opts, &c, &Lc)) { g_err.clear(); continue; }
+    double err = 0.0;
+    if (gate) {
+      Layout Lg;
+      lsp_config c1 = c;
+      c1.obs_split = 1;
+      lsp_opts o1 = p->opts;
+      o1.top_k = 1;
+      o1.norm = LSP_NORM_STANDARD;
+      if (resolve(1, g_n, &p->grid, &o1, &c1, &Lg)) { g_err.clear(); continue; }
+      if ((st = run(Lg, t + g_lo, (const float*)y + g_lo, nullptr, pw, nullptr, gws, s))) { cleanup(); return st; }
+      cudaError_t e = launch_max_abs_diff(pw, ref, p->grid.n_f, d_err, s);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(&err, d_err, sizeof(double), cudaMemcpyDeviceToHost, s);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+      if (e != cudaSuccess) { cleanup(); return cuda_fail(e, "autotune gate"); }
+      if (!(err <= 1e-4)) continue;
+    }
+    if ((st = ensure_ws(p, Lc.total))) { cleanup(); return st; }
+    Layout saved = p->L;
+    p->L = Lc;
+    float ms = 0.f;
+    st = time_runs(p, t, y, offsets, 3, s, &ms);
+    p->L = saved;
+    if (st) { cleanup(); return st; }
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = config_of(Lc);
+      best_err = err;
+      any = true;
+    }
+  }
+  cleanup();
+  if (!any) return fail(LSP_E_NUMERIC, "no candidate configuration passed the error gate");
+  if ((st = apply_config(p, &best))) return st;
+  if (cache_path) cache_store(cache_path, key, best, best_ms, best_err);
+  return LSP_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,288 @@
+// lsp_common.cuh -- data layout and device helpers shared by the kernels of
+// the GB300 Lomb-Scargle library (internal; not part of the C ABI).
+//
+// HBM layout of one call's workspace (all sections 256-byte aligned):
+//   ObjInfo  obj[n_obj]                 per-object statistics (prologue)
+//   Rec      rec[total_nt]              per-observation records (prologue)
+//   int32    order[n_obj]               objects by decreasing N_t (LPT queue)
+//   uint32   hist[LSP_HIST_BINS + 1]    counting-sort scratch
+//   uint32   queue[4]                   persistent-kernel work counter
+//   ChunkBest best[n_obj * n_chunks]    first maximum of each frequency chunk
+//   ChunkCand cand[n_obj * n_chunks]    top-3 local maxima + edge bins (top_k > 1)
+//   partial  part[split * n_f]          split-N_t partial sums (single object)
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#define LSP_HIST_BINS 4096
+#define LSP_TILE_OBS 256
+
+namespace lsp {
+
+// Per-object statistics written by the prologue (Section 2: zero-mean y).
+struct __align__(16) ObjInfo {
+  double t0;         // midpoint of the object's time span; phases use t - t0
+  double ymean;      // FP64 mean of y (0 when centring is off)
+  double sum_y2;     // FP64 sum of the centred y^2
+  int64_t begin;     // offsets[o]
+  int32_t n;         // N_t (0 for an object with bad offsets)
+  int32_t flags;     // LSP_FLAG_*
+  double norm_scale; // 2 / sum_y2 (standard normalisation) or 1 (PSD)
+};
+
+// FP32 path record, 32 bytes.  Phase of frequency k at this observation, in
+// cycles, is frac(a + k b) with a = f_min (t - t0) and b = df (t - t0), both
+// held as 64-bit fixed point (2^64 = one cycle).  (cr, sr) rotate the phase
+// by one grid step: cos/sin(2 pi df (t - t0)).
+struct __align__(16) RecF32 {
+  float y;   // centred magnitude
+  float cr;  // cos(2 pi b)
+  float sr;  // sin(2 pi b)
+  uint32_t a_hi;
+  uint32_t b_hi;
+  uint32_t b_lo;
+  uint32_t a_lo;
+  uint32_t pad;
+};
+
+// FP64 path record, 48 bytes.
+struct __align__(16) RecF64 {
+  double y;
+  double cr;
+  double sr;
+  uint64_t a;
+  uint64_t b;
+  uint64_t pad;
+};
+
+// First maximum of one frequency chunk (lowest index on ties).
+struct __align__(16) ChunkBest {
+  double p;
+  int64_t k;  // -1: empty chunk
+};
+
+// Top-3 interior local maxima of a chunk plus its edge bins, from which the
+// finalize kernel resolves maxima that straddle chunk boundaries.
+struct __align__(16) ChunkCand {
+  double p[3];
+  int64_t k[3];      // -1: none
+  double first[2];   // powers of the chunk's first two bins
+  double last[2];    // powers of the last bin and the one before it
+  int64_t k_first;   // index of the first bin
+  int32_t nvalid;    // bins of the chunk inside the grid
+  int32_t pad;
+};
+
+// Main-kernel parameters.
+template <typename Rec, typename Real>
+struct MainParams {
+  const Rec* rec;
+  const ObjInfo* obj;
+  const int32_t* order;  // LPT object order (nullptr: identity)
+  Real* power_out;       // nullable, n_obj x n_f
+  Real* part;            // split partials (4 per frequency), nullable
+  ChunkBest* best;
+  ChunkCand* cand;       // nullable: only with top_k > 1
+  uint32_t* queue;
+  int64_t n_f;
+  int32_t n_chunks;      // frequency chunks per object
+  int32_t split;         // observation splits per chunk (1 = fused epilogue)
+  int64_t n_items;       // n_obj * n_chunks * split
+};
+
+// ---------------------------------------------------------------- f32x2 ops
+// Packed FP32 pairs (two reseed chains side by side).  Each instruction does
+// two FP32 operations, halving the issue slots of the hot loop.
+typedef unsigned long long f2_t;
+
+__device__ __forceinline__ f2_t f2_pack(float lo, float hi) {
+  f2_t r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+__device__ __forceinline__ void f2_unpack(f2_t v, float& lo, float& hi) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ f2_t f2_fma(f2_t a, f2_t b, f2_t c) {
+  f2_t d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+__device__ __forceinline__ f2_t f2_mul(f2_t a, f2_t b) {
+  f2_t d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+
+// ------------------------------------------------------------ phase seeds
+// High 32 bits of (a + k b) mod 2^64 from a_hi, b_hi, b_lo: the fraction of
+// a cycle as a 32-bit fixed-point number (the carry out of the low word is
+// dropped: error <= 2^-32 cycle).
+__device__ __forceinline__ uint32_t phase_hi32(uint32_t a_hi, uint32_t b_hi, uint32_t b_lo,
+                                               uint32_t k) {
+  return a_hi + k * b_hi + __umulhi(k, b_lo);
+}
+
+// (cos, sin) of a 32-bit fixed-point phase, on the SFU.  The phase is read as
+// a signed fraction in [-1/2, 1/2) cycle so the hardware sine sees an
+// argument in [-pi, pi), where its absolute error is about 2^-21.4.
+__device__ __forceinline__ void seed_sincos_f32(uint32_t ph, float& c, float& s) {
+  const float scale = 6.28318530717958647692f * 2.3283064365386963e-10f;  // 2 pi / 2^32
+  float x = __int2float_rn((int)ph) * scale;
+  __sincosf(x, &s, &c);
+}
+
+// (cos, sin) of a 64-bit fixed-point phase in FP64 (accurate library sincospi).
+__device__ __forceinline__ void seed_sincos_f64(uint64_t ph, double& c, double& s) {
+  double x = (double)(int64_t)ph * 5.421010862427522e-20;  // 2^-64: cycles in [-1/2, 1/2)
+  sincospi(2.0 * x, &s, &c);
+}
+
+// --------------------------------------------------------- power (Eq. 1-2)
+// Eq. 2 evaluated from single-scan sums (the refactoring of Section 2):
+//   Z = XC + i XS = sum y e^{i phi},  W = (2 CC - N) + i 2 CS = sum e^{2 i phi}.
+// With R = |W|, Eq. 1's tau satisfies e^{2 i w tau} = W / R, the tau-shifted
+// denominators are (N + R)/2 and (N - R)/2, and with Q = Re(Z^2 conj(W)) / R
+// the tau-shifted numerators are (|Z|^2 + Q)/2 and (|Z|^2 - Q)/2, so
+//   P = 1/2 [ (|Z|^2 + Q) / (N + R) + (|Z|^2 - Q) / (N - R) ].
+// A term whose denominator (N +- R)/2 is at or below eps_rel * N is dropped
+// (the Eq. 2 sum vanishes there); atan2(0, 0) = 0 corresponds to Q = 0.
+template <typename Real>
+__device__ __forceinline__ Real lsp_power(Real xc, Real xs, Real cc, Real cs, Real n,
+                                          Real eps_rel) {
+  Real c2 = Real(2) * cc - n;
+  Real s2 = Real(2) * cs;
+  Real r = sqrt(c2 * c2 + s2 * s2);
+  Real z2 = xc * xc + xs * xs;
+  Real q = r > Real(0) ? ((xc * xc - xs * xs) * c2 + Real(2) * xc * xs * s2) / r : Real(0);
+  Real eps = eps_rel * n;
+  Real p = Real(0);
+  Real d1 = n + r, d2 = n - r;
+  Real n1 = z2 + q, n2 = z2 - q;
+  if (Real(0.5) * d1 > eps) p += (n1 > Real(0) ? n1 : Real(0)) / d1;
+  if (Real(0.5) * d2 > eps) p += (n2 > Real(0) ? n2 : Real(0)) / d2;
+  return Real(0.5) * p;
+}
+
+template <typename Real> struct EpsRel;
+template <> struct EpsRel<float> { static constexpr float v = 1e-6f; };
+template <> struct EpsRel<double> { static constexpr double v = 1e-12; };
+
+// ------------------------------------------------------ chunk reductions
+// (p, k) pair ordering: higher power first, lower index on ties.
+__device__ __forceinline__ bool better(double pa, int64_t ka, double pb, int64_t kb) {
+  if (ka < 0) return false;
+  if (kb < 0) return true;
+  return pa > pb || (pa == pb && ka < kb);
+}
+
+__device__ __forceinline__ void warp_best(double& p, int64_t& k) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    double po = __shfl_xor_sync(0xffffffffu, p, off);
+    long long ko = __shfl_xor_sync(0xffffffffu, (long long)k, off);
+    if (better(po, ko, p, k)) {
+      p = po;
+      k = ko;
+    }
+  }
+}
+
+// Block-wide best (p, k); every thread gets the result.  `red` needs
+// 2 * (blockDim.x / 32) 8-byte slots.  Contains __syncthreads.
+__device__ __forceinline__ void block_best(double& p, int64_t& k, double* red_p, int64_t* red_k) {
+  warp_best(p, k);
+  int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  if (lane == 0) {
+    red_p[warp] = p;
+    red_k[warp] = k;
+  }
+  __syncthreads();
+  p = lane < nw ? red_p[lane] : 0.0;
+  k = lane < nw ? red_k[lane] : -1;
+  warp_best(p, k);
+  __syncthreads();
+}
+
+// Reduce the chunk's powers (each thread holds NP consecutive bins starting
+// at k0, `nv` of them inside the grid) to its first maximum and, when cand
+// is not null, to its top-3 interior local maxima and edge bins.  `pw` is a
+// shared buffer of blockDim.x * NP floats/doubles (only used with cand).
+template <typename Real, int NP>
+__device__ void chunk_results(const Real (&pv)[NP], int64_t k0, int64_t k_chunk0, int64_t n_f,
+                              ChunkBest* best_out, ChunkCand* cand_out, Real* pw, double* red_p,
+                              int64_t* red_k) {
+  double bp = 0.0;
+  int64_t bk = -1;
+#pragma unroll
+  for (int m = 0; m < NP; ++m) {
+    int64_t k = k0 + m;
+    if (k < n_f && better((double)pv[m], k, bp, bk)) {
+      bp = (double)pv[m];
+      bk = k;
+    }
+  }
+  if (cand_out == nullptr) {
+    block_best(bp, bk, red_p, red_k);
+    if (threadIdx.x == 0) *best_out = ChunkBest{bp, bk};
+    return;
+  }
+  // top-k path: stage the chunk's powers in shared memory
+  const int chunk_len = blockDim.x * NP;
+  int64_t nvalid64 = n_f - k_chunk0;
+  int nvalid = nvalid64 < chunk_len ? (int)nvalid64 : chunk_len;
+  int base = threadIdx.x * NP;
+#pragma unroll
+  for (int m = 0; m < NP; ++m) pw[base + m] = pv[m];
+  __syncthreads();
+  // per-thread top-3 of interior local maxima (bins 1 .. nvalid-2 of the chunk)
+  double tp[3] = {0.0, 0.0, 0.0};
+  int64_t tk[3] = {-1, -1, -1};
+#pragma unroll
+  for (int m = 0; m < NP; ++m) {
+    int i = base + m;
+    if (i >= 1 && i <= nvalid - 2) {
+      Real v = pw[i];
+      if (v > pw[i - 1] && v >= pw[i + 1]) {
+        double dv = (double)v;
+        int64_t k = k_chunk0 + i;
+        if (better(dv, k, tp[0], tk[0])) {
+          tp[2] = tp[1]; tk[2] = tk[1]; tp[1] = tp[0]; tk[1] = tk[0]; tp[0] = dv; tk[0] = k;
+        } else if (better(dv, k, tp[1], tk[1])) {
+          tp[2] = tp[1]; tk[2] = tk[1]; tp[1] = dv; tk[1] = k;
+        } else if (better(dv, k, tp[2], tk[2])) {
+          tp[2] = dv; tk[2] = k;
+        }
+      }
+    }
+  }
+  // three rounds of block arg-best, each removing the winner from its owner
+  ChunkCand out;
+  for (int r = 0; r < 3; ++r) {
+    double p = tp[0];
+    int64_t k = tk[0];
+    block_best(p, k, red_p, red_k);
+    out.p[r] = p;
+    out.k[r] = k;
+    if (k >= 0 && tk[0] == k) {
+      tp[0] = tp[1]; tk[0] = tk[1]; tp[1] = tp[2]; tk[1] = tk[2]; tp[2] = 0.0; tk[2] = -1;
+    }
+  }
+  // the chunk's first maximum over all its bins
+  block_best(bp, bk, red_p, red_k);
+  if (threadIdx.x == 0) {
+    *best_out = ChunkBest{bp, bk};
+    out.k_first = k_chunk0;
+    out.nvalid = nvalid;
+    out.pad = 0;
+    out.first[0] = nvalid > 0 ? (double)pw[0] : 0.0;
+    out.first[1] = nvalid > 1 ? (double)pw[1] : 0.0;
+    out.last[0] = nvalid > 0 ? (double)pw[nvalid - 1] : 0.0;
+    out.last[1] = nvalid > 1 ? (double)pw[nvalid - 2] : 0.0;
+    *cand_out = out;
+  }
+  __syncthreads();
+}
+
+}  // namespace lsp

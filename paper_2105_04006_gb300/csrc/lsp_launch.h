@@ -1,0 +1,76 @@
+// lsp_launch.h -- host-side launchers of the library's kernels (internal).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "lsp_common.cuh"
+
+struct lsp_peak;
+
+namespace lsp {
+
+// Prologue, Section 2 (zero-mean magnitudes) and the per-observation phase
+// data of the rotation recurrence.  y is float (y64 = false) or double.
+cudaError_t launch_stats(const double* t, const void* y, bool y64, const int64_t* offsets,
+                         int64_t n_obj, int64_t total_nt, int center, int norm, ObjInfo* obj,
+                         cudaStream_t stream);
+cudaError_t launch_records(const double* t, const void* y, bool y64, const ObjInfo* obj,
+                           int64_t n_obj, int64_t max_nt_single, double f_min, double df,
+                           bool rec64, void* rec, cudaStream_t stream);
+// Objects ordered by decreasing N_t (counting sort).
+cudaError_t launch_lpt_order(const ObjInfo* obj, int64_t n_obj, uint32_t* hist, int32_t* order,
+                             cudaStream_t stream);
+
+// Main kernel variants.
+struct MainLaunch {
+  int prec;      // 0 FP32, 1 FP64
+  int packed;    // FP32 only
+  int k_reseed;  // chain length K
+  int fpt;       // frequencies per thread (packed: 2K; scalar: K)
+  int threads;
+  int grid;      // persistent CTAs
+  int top;       // 1: top-k candidates
+  const void* rec;
+  const ObjInfo* obj;
+  const int32_t* order;
+  void* power_out;
+  void* part;
+  ChunkBest* best;
+  ChunkCand* cand;
+  uint32_t* queue;
+  int64_t n_f;
+  int32_t n_chunks;
+  int32_t split;
+  int64_t n_items;
+};
+bool main_variant_exists(int prec, int packed, int k_reseed, int fpt);
+cudaError_t launch_main(const MainLaunch& ml, cudaStream_t stream);
+// CTAs of the main variant resident per SM (0 if the variant does not exist).
+int main_blocks_per_sm(int prec, int packed, int k_reseed, int fpt, int threads, int top);
+size_t main_dyn_smem(int prec, int fpt, int threads, int top);
+
+// Split-N_t combine (single object): sums the partial sums in a fixed order,
+// evaluates the power, stores it (optional) and reduces chunk results.
+constexpr int kCombineThreads = 256;
+constexpr int kCombinePerThread = 4;
+cudaError_t launch_combine(int prec, const void* part, int split, int64_t n_f, const ObjInfo* obj,
+                           void* power_out, ChunkBest* best, ChunkCand* cand, cudaStream_t stream);
+
+// Per-object peaks from the chunk results.
+cudaError_t launch_finalize(const ObjInfo* obj, const ChunkBest* best, const ChunkCand* cand,
+                            int64_t n_obj, int n_chunks, int top_k, double f_min, double df,
+                            lsp_peak* peaks, cudaStream_t stream);
+
+// First maximum of stored periodograms (no workspace: the peak records hold
+// the reduction state).
+cudaError_t launch_argmax_period(const void* power, bool p64, int64_t n_obj, int64_t n_f,
+                                 double f_min, double df, lsp_peak* peaks, cudaStream_t stream);
+
+// Autotuner error gate helpers.
+cudaError_t launch_f32_to_f64(const float* a, double* b, int64_t n, cudaStream_t stream);
+cudaError_t launch_max_abs_diff(const float* a, const double* b, int64_t n, double* out,
+                                cudaStream_t stream);
+
+}  // namespace lsp

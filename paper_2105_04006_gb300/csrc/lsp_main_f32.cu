@@ -1,0 +1,76 @@
+// lsp_main_f32.cu -- instantiations of the FP32 trig-sum kernels.
+#include "lsp_launch.h"
+#include "lsp_main_impl.cuh"
+
+namespace lsp {
+
+namespace {
+template <typename Kern, typename P>
+cudaError_t launch_kernel(Kern kern, const MainLaunch& ml, const P& p, cudaStream_t stream) {
+  size_t dyn = main_dyn_smem(ml.prec, ml.fpt, ml.threads, ml.top);
+  if (dyn > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+    if (e != cudaSuccess) return e;
+  }
+  kern<<<ml.grid, ml.threads, dyn, stream>>>(p);
+  return cudaGetLastError();
+}
+
+template <typename Kern>
+int occupancy(Kern kern, int threads, size_t dyn) {
+  int nb = 0;
+  if (dyn > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, threads, dyn) != cudaSuccess) return 0;
+  return nb;
+}
+
+template <typename Fn>
+bool dispatch_f32(int packed, int k, Fn&& fn) {
+  if (packed) {
+    switch (k) {
+      case 4: fn(main_f32_packed<4>); return true;
+      case 8: fn(main_f32_packed<8>); return true;
+      case 16: fn(main_f32_packed<16>); return true;
+    }
+  } else {
+    switch (k) {
+      case 8: fn(main_scalar<float, RecF32, 8>); return true;
+      case 16: fn(main_scalar<float, RecF32, 16>); return true;
+    }
+  }
+  return false;
+}
+}  // namespace
+
+bool main_variant_exists_f32(int packed, int k, int fpt) {
+  if (fpt != (packed ? 2 * k : k)) return false;
+  return dispatch_f32(packed, k, [](auto) {});
+}
+
+int main_blocks_per_sm_f32(int packed, int k, int fpt, int threads, int top) {
+  int nb = 0;
+  size_t dyn = main_dyn_smem(0, fpt, threads, top);
+  dispatch_f32(packed, k, [&](auto kern) { nb = occupancy(kern, threads, dyn); });
+  return nb;
+}
+
+cudaError_t launch_main_f32(const MainLaunch& ml, cudaStream_t stream) {
+  MainParams<RecF32, float> p;
+  p.rec = (const RecF32*)ml.rec;
+  p.obj = ml.obj;
+  p.order = ml.order;
+  p.power_out = (float*)ml.power_out;
+  p.part = (float*)ml.part;
+  p.best = ml.best;
+  p.cand = ml.cand;
+  p.queue = ml.queue;
+  p.n_f = ml.n_f;
+  p.n_chunks = ml.n_chunks;
+  p.split = ml.split;
+  p.n_items = ml.n_items;
+  cudaError_t err = cudaErrorInvalidValue;
+  dispatch_f32(ml.packed, ml.k_reseed, [&](auto kern) { err = launch_kernel(kern, ml, p, stream); });
+  return err;
+}
+
+}  // namespace lsp

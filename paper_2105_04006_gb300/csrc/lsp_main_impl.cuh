@@ -1,0 +1,274 @@
+// lsp_main_impl.cuh -- the trig-sum kernels (internal).
+//
+// What they compute: for every object o and grid frequency k the single-scan
+// sums of Section 2 (the refactoring the paper ports from SciPy, Listing 1):
+//   XC = sum_j y_j cos phi_jk,  XS = sum_j y_j sin phi_jk,
+//   CC = sum_j cos^2 phi_jk,    CS = sum_j cos phi_jk sin phi_jk,
+// with phi_jk = 2 pi f_k (t_j - t0); sum sin^2 = N - CC.  The epilogue turns
+// them into Eq. 2's power (lsp_power) and reduces each chunk of frequencies
+// to its maximum, so the periodogram reaches HBM only on request.
+//
+// How (the GB300 design; the paper's one-thread-per-frequency kernel with a
+// library sincos per pair is prior art):
+//   - a CTA owns a chunk of blockDim.x * F consecutive frequencies of one
+//     object; each thread owns F consecutive frequencies of it;
+//   - observations are staged through shared memory in tiles and read by
+//     all threads at once (broadcast), so every (t, y) load is shared by the
+//     CTA's blockDim.x * F frequencies;
+//   - sin/cos come from a rotation recurrence across the uniform grid,
+//     (c, s) <- (c cr - s sr, s cr + c sr) with (cr, sr) = e^{2 pi i df t'},
+//     reseeded from the exact fixed-point phase every K frequencies (the
+//     paper, Section 4.5, rejects the recurrence as serial; here it runs
+//     along a thread's own frequencies while threads, CTAs and objects run
+//     in parallel);
+//   - the FP32 kernel packs two reseed chains into f32x2 lanes, so one
+//     instruction advances two frequencies;
+//   - CTAs are persistent and pull (object, chunk, split) items from a queue
+//     ordered by decreasing N_t.
+#pragma once
+
+#include <type_traits>
+
+#include "lsp_common.cuh"
+
+namespace lsp {
+
+template <int F>
+__device__ __forceinline__ void store_row(float* row, int64_t k0, const float (&pv)[F], int64_t n_f) {
+  if (k0 + F <= n_f && ((reinterpret_cast<uintptr_t>(row + k0) & 15) == 0)) {
+    float4* d = reinterpret_cast<float4*>(row + k0);
+#pragma unroll
+    for (int q = 0; q < F / 4; ++q)
+      __stcs(d + q, make_float4(pv[4 * q], pv[4 * q + 1], pv[4 * q + 2], pv[4 * q + 3]));
+  } else {
+#pragma unroll
+    for (int m = 0; m < F; ++m)
+      if (k0 + m < n_f) row[k0 + m] = pv[m];
+  }
+}
+
+template <int F>
+__device__ __forceinline__ void store_row(double* row, int64_t k0, const double (&pv)[F], int64_t n_f) {
+  if (k0 + F <= n_f && ((reinterpret_cast<uintptr_t>(row + k0) & 15) == 0)) {
+    double2* d = reinterpret_cast<double2*>(row + k0);
+#pragma unroll
+    for (int q = 0; q < F / 2; ++q) __stcs(d + q, make_double2(pv[2 * q], pv[2 * q + 1]));
+  } else {
+#pragma unroll
+    for (int m = 0; m < F; ++m)
+      if (k0 + m < n_f) row[k0 + m] = pv[m];
+  }
+}
+
+__device__ __forceinline__ void store_part(float* part, int64_t idx, float a, float b, float c, float d) {
+  reinterpret_cast<float4*>(part)[idx] = make_float4(a, b, c, d);
+}
+__device__ __forceinline__ void store_part(double* part, int64_t idx, double a, double b, double c,
+                                           double d) {
+  double2* p2 = reinterpret_cast<double2*>(part) + 2 * idx;
+  p2[0] = make_double2(a, b);
+  p2[1] = make_double2(c, d);
+}
+
+// Item decoding shared by the kernels.
+struct Item {
+  int64_t o;
+  int chunk;
+  int s;
+};
+template <typename P>
+__device__ __forceinline__ Item decode_item(const P& p, int64_t item) {
+  Item it;
+  it.s = (int)(item % p.split);
+  const int64_t oc = item / p.split;
+  it.chunk = (int)(oc % p.n_chunks);
+  const int64_t orank = oc / p.n_chunks;
+  it.o = p.order ? (int64_t)p.order[orank] : orank;
+  return it;
+}
+
+// ------------------------------------------------------------------------
+// FP32, two reseed chains of K frequencies per thread in packed f32x2 lanes:
+// lane 0 covers k0 .. k0+K-1, lane 1 covers k0+K .. k0+2K-1.
+template <int K>
+__global__ void __launch_bounds__(256) main_f32_packed(MainParams<RecF32, float> p) {
+  constexpr int F = 2 * K;
+  __shared__ uint4 s_rec[2 * LSP_TILE_OBS];
+  __shared__ double red_p[32];
+  __shared__ int64_t red_k[32];
+  __shared__ uint32_t s_item;
+  extern __shared__ __align__(16) unsigned char dyn_smem[];
+  float* s_pw = reinterpret_cast<float*>(dyn_smem);
+  const int tid = threadIdx.x;
+
+  for (;;) {
+    if (tid == 0) s_item = atomicAdd(p.queue, 1u);
+    __syncthreads();
+    const int64_t item = s_item;
+    __syncthreads();
+    if (item >= p.n_items) break;
+    const Item it = decode_item(p, item);
+    const ObjInfo oi = p.obj[it.o];
+    const int64_t kc0 = (int64_t)it.chunk * blockDim.x * F;
+    const uint32_t k0 = (uint32_t)(kc0 + (int64_t)tid * F);
+    const uint32_t k1 = k0 + K;
+    int64_t ob = oi.begin + (int64_t)oi.n * it.s / p.split;
+    int64_t oe = oi.begin + (int64_t)oi.n * (it.s + 1) / p.split;
+    if (oi.flags) oe = ob;  // flagged objects: zero power
+
+    f2_t xc[K], xs[K], cc[K], cs[K];
+#pragma unroll
+    for (int m = 0; m < K; ++m) xc[m] = xs[m] = cc[m] = cs[m] = 0ull;
+
+    for (int64_t ts = ob; ts < oe; ts += LSP_TILE_OBS) {
+      const int nt = (int)((oe - ts) < LSP_TILE_OBS ? (oe - ts) : LSP_TILE_OBS);
+      const uint4* src = reinterpret_cast<const uint4*>(p.rec + ts);
+      for (int i = tid; i < 2 * nt; i += blockDim.x) s_rec[i] = __ldg(src + i);
+      __syncthreads();
+      for (int j = 0; j < nt; ++j) {
+        const uint4 r0 = s_rec[2 * j];
+        const uint4 r1 = s_rec[2 * j + 1];
+        const float y = __uint_as_float(r0.x);
+        const float cr = __uint_as_float(r0.y);
+        const float sr = __uint_as_float(r0.z);
+        float c0, s0, c1, s1;
+        seed_sincos_f32(phase_hi32(r0.w, r1.x, r1.y, k0), c0, s0);
+        seed_sincos_f32(phase_hi32(r0.w, r1.x, r1.y, k1), c1, s1);
+        f2_t c2 = f2_pack(c0, c1), s2 = f2_pack(s0, s1);
+        const f2_t y2 = f2_pack(y, y), cr2 = f2_pack(cr, cr);
+        const f2_t sr2 = f2_pack(sr, sr), nsr2 = f2_pack(-sr, -sr);
+#pragma unroll
+        for (int m = 0; m < K; ++m) {
+          xc[m] = f2_fma(y2, c2, xc[m]);
+          xs[m] = f2_fma(y2, s2, xs[m]);
+          cc[m] = f2_fma(c2, c2, cc[m]);
+          cs[m] = f2_fma(c2, s2, cs[m]);
+          if (m + 1 < K) {
+            const f2_t tc = f2_mul(c2, cr2);
+            const f2_t tsr = f2_mul(s2, cr2);
+            const f2_t cn = f2_fma(s2, nsr2, tc);
+            s2 = f2_fma(c2, sr2, tsr);
+            c2 = cn;
+          }
+        }
+      }
+      __syncthreads();
+    }
+
+    if (p.split == 1) {
+      float pv[F];
+      const float nf = (float)oi.n, scale = (float)oi.norm_scale;
+#pragma unroll
+      for (int m = 0; m < K; ++m) {
+        float a0, a1, b0, b1, c0, c1, d0, d1;
+        f2_unpack(xc[m], a0, a1);
+        f2_unpack(xs[m], b0, b1);
+        f2_unpack(cc[m], c0, c1);
+        f2_unpack(cs[m], d0, d1);
+        pv[m] = scale * lsp_power<float>(a0, b0, c0, d0, nf, EpsRel<float>::v);
+        pv[K + m] = scale * lsp_power<float>(a1, b1, c1, d1, nf, EpsRel<float>::v);
+      }
+      if (p.power_out) store_row<F>(p.power_out + it.o * p.n_f, (int64_t)k0, pv, p.n_f);
+      const int64_t res = it.o * p.n_chunks + it.chunk;
+      chunk_results<float, F>(pv, (int64_t)k0, kc0, p.n_f, p.best + res,
+                              p.cand ? p.cand + res : nullptr, s_pw, red_p, red_k);
+    } else {
+      float* part = p.part + (int64_t)it.s * p.n_f * 4;
+#pragma unroll
+      for (int m = 0; m < K; ++m) {
+        float a0, a1, b0, b1, c0, c1, d0, d1;
+        f2_unpack(xc[m], a0, a1);
+        f2_unpack(xs[m], b0, b1);
+        f2_unpack(cc[m], c0, c1);
+        f2_unpack(cs[m], d0, d1);
+        if ((int64_t)k0 + m < p.n_f) store_part(part, (int64_t)k0 + m, a0, b0, c0, d0);
+        if ((int64_t)k1 + m < p.n_f) store_part(part, (int64_t)k1 + m, a1, b1, c1, d1);
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------------------------
+// Scalar kernel: one reseed chain of K frequencies per thread.  Real = float
+// (FP32 records, SFU seeds) or double (FP64 records, FP64 sincospi seeds).
+template <typename Real, typename Rec, int K>
+__global__ void __launch_bounds__(256) main_scalar(MainParams<Rec, Real> p) {
+  constexpr int F = K;
+  constexpr int RW = sizeof(Rec) / 16;
+  __shared__ uint4 s_rec[RW * LSP_TILE_OBS];
+  __shared__ double red_p[32];
+  __shared__ int64_t red_k[32];
+  __shared__ uint32_t s_item;
+  extern __shared__ __align__(16) unsigned char dyn_smem[];
+  Real* s_pw = reinterpret_cast<Real*>(dyn_smem);
+  const int tid = threadIdx.x;
+  const Rec* srec = reinterpret_cast<const Rec*>(s_rec);
+
+  for (;;) {
+    if (tid == 0) s_item = atomicAdd(p.queue, 1u);
+    __syncthreads();
+    const int64_t item = s_item;
+    __syncthreads();
+    if (item >= p.n_items) break;
+    const Item it = decode_item(p, item);
+    const ObjInfo oi = p.obj[it.o];
+    const int64_t kc0 = (int64_t)it.chunk * blockDim.x * F;
+    const uint32_t k0 = (uint32_t)(kc0 + (int64_t)tid * F);
+    int64_t ob = oi.begin + (int64_t)oi.n * it.s / p.split;
+    int64_t oe = oi.begin + (int64_t)oi.n * (it.s + 1) / p.split;
+    if (oi.flags) oe = ob;
+
+    Real xc[K], xs[K], cc[K], cs[K];
+#pragma unroll
+    for (int m = 0; m < K; ++m) xc[m] = xs[m] = cc[m] = cs[m] = Real(0);
+
+    for (int64_t ts = ob; ts < oe; ts += LSP_TILE_OBS) {
+      const int nt = (int)((oe - ts) < LSP_TILE_OBS ? (oe - ts) : LSP_TILE_OBS);
+      const uint4* src = reinterpret_cast<const uint4*>(p.rec + ts);
+      for (int i = tid; i < RW * nt; i += blockDim.x) s_rec[i] = __ldg(src + i);
+      __syncthreads();
+      for (int j = 0; j < nt; ++j) {
+        const Rec r = srec[j];
+        Real c, s;
+        if constexpr (std::is_same<Real, float>::value) {
+          seed_sincos_f32(phase_hi32(r.a_hi, r.b_hi, r.b_lo, k0), c, s);
+        } else {
+          seed_sincos_f64(r.a + (uint64_t)k0 * r.b, c, s);
+        }
+        const Real y = r.y, cr = r.cr, sr = r.sr;
+#pragma unroll
+        for (int m = 0; m < K; ++m) {
+          xc[m] = fma(y, c, xc[m]);
+          xs[m] = fma(y, s, xs[m]);
+          cc[m] = fma(c, c, cc[m]);
+          cs[m] = fma(c, s, cs[m]);
+          if (m + 1 < K) {
+            const Real cn = fma(-s, sr, c * cr);
+            s = fma(c, sr, s * cr);
+            c = cn;
+          }
+        }
+      }
+      __syncthreads();
+    }
+
+    if (p.split == 1) {
+      Real pv[F];
+      const Real nf = (Real)oi.n, scale = (Real)oi.norm_scale;
+#pragma unroll
+      for (int m = 0; m < K; ++m)
+        pv[m] = scale * lsp_power<Real>(xc[m], xs[m], cc[m], cs[m], nf, EpsRel<Real>::v);
+      if (p.power_out) store_row<F>(p.power_out + it.o * p.n_f, (int64_t)k0, pv, p.n_f);
+      const int64_t res = it.o * p.n_chunks + it.chunk;
+      chunk_results<Real, F>(pv, (int64_t)k0, kc0, p.n_f, p.best + res,
+                             p.cand ? p.cand + res : nullptr, s_pw, red_p, red_k);
+    } else {
+      Real* part = p.part + (int64_t)it.s * p.n_f * 4;
+#pragma unroll
+      for (int m = 0; m < K; ++m)
+        if ((int64_t)k0 + m < p.n_f) store_part(part, (int64_t)k0 + m, xc[m], xs[m], cc[m], cs[m]);
+    }
+  }
+}
+
+}  // namespace lsp

@@ -1,0 +1,347 @@
+// lsp_post.cu -- split-N_t combine, per-object peaks, stored-periodogram argmax.
+#include <cmath>
+
+#include "../../include/lsp.h"
+#include "lsp_launch.h"
+
+namespace lsp {
+
+bool main_variant_exists_f32(int packed, int k, int fpt);
+bool main_variant_exists_f64(int k, int fpt);
+int main_blocks_per_sm_f32(int packed, int k, int fpt, int threads, int top);
+int main_blocks_per_sm_f64(int k, int fpt, int threads, int top);
+cudaError_t launch_main_f32(const MainLaunch& ml, cudaStream_t stream);
+cudaError_t launch_main_f64(const MainLaunch& ml, cudaStream_t stream);
+
+size_t main_dyn_smem(int prec, int fpt, int threads, int top) {
+  return top ? (size_t)threads * fpt * (prec ? sizeof(double) : sizeof(float)) : 0;
+}
+
+bool main_variant_exists(int prec, int packed, int k, int fpt) {
+  return prec ? (!packed && main_variant_exists_f64(k, fpt)) : main_variant_exists_f32(packed, k, fpt);
+}
+
+int main_blocks_per_sm(int prec, int packed, int k, int fpt, int threads, int top) {
+  if (!main_variant_exists(prec, packed, k, fpt)) return 0;
+  return prec ? main_blocks_per_sm_f64(k, fpt, threads, top)
+              : main_blocks_per_sm_f32(packed, k, fpt, threads, top);
+}
+
+cudaError_t launch_main(const MainLaunch& ml, cudaStream_t stream) {
+  return ml.prec ? launch_main_f64(ml, stream) : launch_main_f32(ml, stream);
+}
+
+namespace {
+
+// ------------------------------------------------------------- combine
+// Split-N_t single object: sum the S partial sums of each frequency in the
+// fixed order s = 0..S-1 (deterministic), then Eq. 2 and the chunk results.
+template <typename Real>
+__global__ void __launch_bounds__(kCombineThreads) combine_kernel(
+    const Real* __restrict__ part, int split, int64_t n_f, const ObjInfo* __restrict__ obj,
+    Real* __restrict__ power_out, ChunkBest* __restrict__ best, ChunkCand* __restrict__ cand) {
+  constexpr int NP = kCombinePerThread;
+  extern __shared__ __align__(16) unsigned char dyn_smem[];
+  Real* s_pw = reinterpret_cast<Real*>(dyn_smem);
+  __shared__ double red_p[32];
+  __shared__ int64_t red_k[32];
+  const ObjInfo oi = obj[0];
+  const int64_t kc0 = (int64_t)blockIdx.x * blockDim.x * NP;
+  const int64_t k0 = kc0 + (int64_t)threadIdx.x * NP;
+  const Real nf = (Real)oi.n, scale = (Real)oi.norm_scale;
+  Real pv[NP];
+#pragma unroll
+  for (int m = 0; m < NP; ++m) {
+    const int64_t k = k0 + m;
+    Real xc = 0, xs = 0, cc = 0, cs = 0;
+    if (k < n_f && !oi.flags) {
+      for (int s = 0; s < split; ++s) {
+        const Real* q = part + ((int64_t)s * n_f + k) * 4;
+        xc += q[0];
+        xs += q[1];
+        cc += q[2];
+        cs += q[3];
+      }
+    }
+    pv[m] = oi.flags ? Real(0) : scale * lsp_power<Real>(xc, xs, cc, cs, nf, EpsRel<Real>::v);
+  }
+  if (power_out) {
+#pragma unroll
+    for (int m = 0; m < NP; ++m)
+      if (k0 + m < n_f) power_out[k0 + m] = pv[m];
+  }
+  chunk_results<Real, NP>(pv, k0, kc0, n_f, best + blockIdx.x, cand ? cand + blockIdx.x : nullptr,
+                          s_pw, red_p, red_k);
+}
+
+__device__ __forceinline__ lsp_peak make_peak(int64_t k, double p, double f_min, double df,
+                                              int flags) {
+  lsp_peak pk;
+  pk.flags = flags;
+  pk.reserved = 0;
+  if (flags || k < 0) {
+    pk.idx = -1;
+    pk.power = 0.0;
+    pk.freq = 0.0;
+    pk.period = 0.0;
+  } else {
+    pk.idx = k;
+    pk.power = p;
+    pk.freq = __dadd_rn(f_min, __dmul_rn((double)k, df));  // f_min + k df, two roundings
+    pk.period = 1.0 / pk.freq;
+  }
+  return pk;
+}
+
+// First maximum per object: one warp per object, lanes stride the chunks.
+__global__ void finalize_top1(const ObjInfo* __restrict__ obj, const ChunkBest* __restrict__ best,
+                              int64_t n_obj, int n_chunks, double f_min, double df,
+                              lsp_peak* __restrict__ peaks) {
+  const int64_t o = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (o >= n_obj) return;
+  double p = 0.0;
+  int64_t k = -1;
+  for (int c = lane; c < n_chunks; c += 32) {
+    const ChunkBest b = best[o * n_chunks + c];
+    if (better(b.p, b.k, p, k)) {
+      p = b.p;
+      k = b.k;
+    }
+  }
+  warp_best(p, k);
+  if (lane == 0) peaks[o] = make_peak(k, p, f_min, df, obj[o].flags);
+}
+
+__device__ __forceinline__ void top_insert(double (&tp)[3], int64_t (&tk)[3], double p, int64_t k) {
+  if (better(p, k, tp[0], tk[0])) {
+    tp[2] = tp[1]; tk[2] = tk[1]; tp[1] = tp[0]; tk[1] = tk[0]; tp[0] = p; tk[0] = k;
+  } else if (better(p, k, tp[1], tk[1])) {
+    tp[2] = tp[1]; tk[2] = tk[1]; tp[1] = p; tk[1] = k;
+  } else if (better(p, k, tp[2], tk[2])) {
+    tp[2] = p; tk[2] = k;
+  }
+}
+
+// Top-k local maxima per object: merge the chunks' interior candidates and
+// resolve each chunk's first and last bin against its neighbour chunks.  A
+// bin is a local maximum when P[k] > P[k-1] and P[k] >= P[k+1]; the grid
+// ends compare with their one neighbour.
+__global__ void finalize_topk(const ObjInfo* __restrict__ obj, const ChunkCand* __restrict__ cand,
+                              int64_t n_obj, int n_chunks, int top_k, double f_min, double df,
+                              lsp_peak* __restrict__ peaks) {
+  const int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (o >= n_obj) return;
+  const ChunkCand* cc = cand + o * n_chunks;
+  double tp[3] = {0.0, 0.0, 0.0};
+  int64_t tk[3] = {-1, -1, -1};
+  const double lo_inf = -INFINITY;
+  for (int c = 0; c < n_chunks; ++c) {
+    const ChunkCand x = cc[c];
+    if (x.nvalid <= 0) continue;
+    for (int r = 0; r < 3; ++r)
+      if (x.k[r] >= 0) top_insert(tp, tk, x.p[r], x.k[r]);
+    const double next_first = (c + 1 < n_chunks && cc[c + 1].nvalid > 0) ? cc[c + 1].first[0] : lo_inf;
+    const double prev_last = c > 0 ? cc[c - 1].last[0] : lo_inf;
+    // first bin of the chunk
+    {
+      const double v = x.first[0];
+      const double right = x.nvalid >= 2 ? x.first[1] : next_first;
+      if (v > prev_last && v >= right) top_insert(tp, tk, v, x.k_first);
+    }
+    // last bin of the chunk
+    if (x.nvalid >= 2) {
+      const double v = x.last[0];
+      if (v > x.last[1] && v >= next_first) top_insert(tp, tk, v, x.k_first + x.nvalid - 1);
+    }
+  }
+  const int flags = obj[o].flags;
+  for (int r = 0; r < top_k; ++r) peaks[o * top_k + r] = make_peak(tk[r], tp[r], f_min, df, flags);
+}
+
+// ------------------------------------------- argmax of a stored periodogram
+// Section 3.3 computes the period with a separate reduction over the stored
+// periodogram.  The reduction state lives in the output records: pass 1 takes
+// the maximum of an order-preserving 64-bit key of each power (in the
+// power field), pass 2 the minimum index attaining it (in the idx field).
+__device__ __forceinline__ unsigned long long order_key(double v) {
+  unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+__device__ __forceinline__ double key_value(unsigned long long key) {
+  unsigned long long b = (key >> 63) ? (key & 0x7fffffffffffffffull) : ~key;
+  return __longlong_as_double((long long)b);
+}
+
+__global__ void am_init(int64_t n_obj, lsp_peak* peaks) {
+  const int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (o >= n_obj) return;
+  lsp_peak pk;
+  pk.idx = INT64_MAX;
+  pk.power = __longlong_as_double(0);  // key 0: below every non-NaN value
+  pk.freq = 0.0;
+  pk.period = 0.0;
+  pk.flags = 0;
+  pk.reserved = 0;
+  peaks[o] = pk;
+}
+
+template <typename Real>
+__device__ __forceinline__ unsigned long long block_max_u64(unsigned long long v, unsigned long long* sh) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    unsigned long long w = __shfl_xor_sync(0xffffffffu, v, off);
+    v = w > v ? w : v;
+  }
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  if (lane == 0) sh[wid] = v;
+  __syncthreads();
+  v = lane < nw ? sh[lane] : 0ull;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    unsigned long long w = __shfl_xor_sync(0xffffffffu, v, off);
+    v = w > v ? w : v;
+  }
+  return v;
+}
+
+// grid: (row blocks, object slices); each CTA reduces a contiguous row range.
+template <typename Real, int PASS>
+__global__ void am_pass(const Real* __restrict__ power, int64_t n_obj, int64_t n_f, int64_t per_cta,
+                        lsp_peak* peaks) {
+  __shared__ unsigned long long sh[32];
+  for (int64_t o = blockIdx.y; o < n_obj; o += gridDim.y) {
+    const Real* row = power + o * n_f;
+    const int64_t lo = (int64_t)blockIdx.x * per_cta;
+    int64_t hi = lo + per_cta;
+    if (hi > n_f) hi = n_f;
+    unsigned long long* keyp = reinterpret_cast<unsigned long long*>(&peaks[o].power);
+    if (PASS == 1) {
+      unsigned long long best = 0ull;
+      for (int64_t k = lo + threadIdx.x; k < hi; k += blockDim.x) {
+        const double v = (double)row[k];
+        if (!isnan(v)) {
+          const unsigned long long key = order_key(v);
+          best = key > best ? key : best;
+        }
+      }
+      best = block_max_u64<Real>(best, sh);
+      if (threadIdx.x == 0 && best) atomicMax(keyp, best);
+    } else {
+      const unsigned long long target = *keyp;
+      unsigned long long mk = ~0ull;  // minimum index, as the max of its complement
+      for (int64_t k = lo + threadIdx.x; k < hi; k += blockDim.x) {
+        const double v = (double)row[k];
+        if (!isnan(v) && order_key(v) == target) {
+          mk = (unsigned long long)k < mk ? (unsigned long long)k : mk;
+        }
+      }
+      unsigned long long inv = block_max_u64<Real>(~mk, sh);
+      if (threadIdx.x == 0 && inv) atomicMin(reinterpret_cast<unsigned long long*>(&peaks[o].idx), ~inv);
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void am_decode(int64_t n_obj, double f_min, double df, lsp_peak* peaks) {
+  const int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (o >= n_obj) return;
+  lsp_peak pk = peaks[o];
+  const unsigned long long key = (unsigned long long)__double_as_longlong(pk.power);
+  if (pk.idx == INT64_MAX || key == 0ull) {
+    peaks[o] = make_peak(-1, 0.0, f_min, df, 0);
+    return;
+  }
+  peaks[o] = make_peak(pk.idx, key_value(key), f_min, df, 0);
+}
+
+__global__ void f32_to_f64_kernel(const float* __restrict__ a, double* __restrict__ b, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    b[i] = (double)a[i];
+}
+
+// max_i |a_i - b_i| into *out (a non-negative double updated through its bits).
+__global__ void max_abs_diff_kernel(const float* __restrict__ a, const double* __restrict__ b, int64_t n,
+                                    unsigned long long* out) {
+  __shared__ unsigned long long sh[32];
+  unsigned long long m = 0ull;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    double d = fabs((double)a[i] - b[i]);
+    if (isnan(d)) d = INFINITY;
+    unsigned long long v = (unsigned long long)__double_as_longlong(d);
+    m = v > m ? v : m;
+  }
+  m = block_max_u64<double>(m, sh);
+  if (threadIdx.x == 0) atomicMax(out, m);
+}
+
+}  // namespace
+
+cudaError_t launch_f32_to_f64(const float* a, double* b, int64_t n, cudaStream_t stream) {
+  if (n <= 0) return cudaSuccess;
+  f32_to_f64_kernel<<<1024, 256, 0, stream>>>(a, b, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_max_abs_diff(const float* a, const double* b, int64_t n, double* out, cudaStream_t stream) {
+  cudaError_t e = cudaMemsetAsync(out, 0, sizeof(double), stream);
+  if (e != cudaSuccess || n <= 0) return e;
+  max_abs_diff_kernel<<<512, 256, 0, stream>>>(a, b, n, reinterpret_cast<unsigned long long*>(out));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_combine(int prec, const void* part, int split, int64_t n_f, const ObjInfo* obj,
+                           void* power_out, ChunkBest* best, ChunkCand* cand, cudaStream_t stream) {
+  const int64_t per_cta = (int64_t)kCombineThreads * kCombinePerThread;
+  const unsigned grid = (unsigned)((n_f + per_cta - 1) / per_cta);
+  const size_t dyn = cand ? (size_t)per_cta * (prec ? 8 : 4) : 0;
+  if (prec)
+    combine_kernel<double><<<grid, kCombineThreads, dyn, stream>>>(
+        (const double*)part, split, n_f, obj, (double*)power_out, best, cand);
+  else
+    combine_kernel<float><<<grid, kCombineThreads, dyn, stream>>>(
+        (const float*)part, split, n_f, obj, (float*)power_out, best, cand);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_finalize(const ObjInfo* obj, const ChunkBest* best, const ChunkCand* cand,
+                            int64_t n_obj, int n_chunks, int top_k, double f_min, double df,
+                            lsp_peak* peaks, cudaStream_t stream) {
+  if (n_obj <= 0 || peaks == nullptr) return cudaSuccess;
+  if (top_k <= 1 || cand == nullptr) {
+    const int64_t threads = 256, warps_per_cta = threads / 32;
+    const unsigned grid = (unsigned)((n_obj + warps_per_cta - 1) / warps_per_cta);
+    finalize_top1<<<grid, (unsigned)threads, 0, stream>>>(obj, best, n_obj, n_chunks, f_min, df, peaks);
+  } else {
+    const unsigned grid = (unsigned)((n_obj + 127) / 128);
+    finalize_topk<<<grid, 128, 0, stream>>>(obj, cand, n_obj, n_chunks, top_k, f_min, df, peaks);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_argmax_period(const void* power, bool p64, int64_t n_obj, int64_t n_f,
+                                 double f_min, double df, lsp_peak* peaks, cudaStream_t stream) {
+  if (n_obj <= 0) return cudaSuccess;
+  const unsigned g1 = (unsigned)((n_obj + 255) / 256);
+  am_init<<<g1, 256, 0, stream>>>(n_obj, peaks);
+  const int threads = 256;
+  int64_t per_cta = 8192;
+  int64_t gx = (n_f + per_cta - 1) / per_cta;
+  if (gx > 65535) {
+    gx = 65535;
+    per_cta = (n_f + gx - 1) / gx;
+  }
+  const unsigned gy = (unsigned)(n_obj < 65535 ? n_obj : 65535);
+  dim3 grid((unsigned)gx, gy);
+  if (p64) {
+    am_pass<double, 1><<<grid, threads, 0, stream>>>((const double*)power, n_obj, n_f, per_cta, peaks);
+    am_pass<double, 2><<<grid, threads, 0, stream>>>((const double*)power, n_obj, n_f, per_cta, peaks);
+  } else {
+    am_pass<float, 1><<<grid, threads, 0, stream>>>((const float*)power, n_obj, n_f, per_cta, peaks);
+    am_pass<float, 2><<<grid, threads, 0, stream>>>((const float*)power, n_obj, n_f, per_cta, peaks);
+  }
+  am_decode<<<g1, 256, 0, stream>>>(n_obj, f_min, df, peaks);
+  return cudaGetLastError();
+}
+
+}  // namespace lsp

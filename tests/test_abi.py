@@ -1,0 +1,126 @@
+"""CPU-only checks of the C-ABI library: it builds for sm_103a, loads, exports
+every function that include/lsp.h declares, and validates arguments on the
+host (these calls return before anything would be launched)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="session")
+def lsp_mod():
+    from paper_2105_04006_gb300 import build
+    build.build()
+    import paper_2105_04006_gb300 as lsp
+    return lsp
+
+
+def _declared_functions():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if not fn.endswith(".h"):
+            continue
+        src = open(os.path.join(ROOT, "include", fn)).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        for m in re.finditer(r"^\s*[A-Za-z_][\w\s\*]*?\b(lsp_\w+)\s*\(", src, flags=re.M):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+def test_every_declared_symbol_is_exported(lsp_mod):
+    names = _declared_functions()
+    assert "lsp_batch" in names and "lsp_periodogram" in names and "lsp_argmax_period" in names
+    lib = ctypes.CDLL(lsp_mod.LIB_PATH)
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, f"declared but not exported: {missing}"
+    # and the binding knows all of them
+    assert set(names) <= set(lsp_mod.EXPORTS), set(names) - set(lsp_mod.EXPORTS)
+
+
+def test_library_is_built_for_sm103a(lsp_mod):
+    data = open(lsp_mod.LIB_PATH, "rb").read()
+    assert b"sm_103a" in data or b"sm_103" in data
+
+
+def test_status_strings_and_defaults(lsp_mod):
+    L = lsp_mod.lib()
+    assert L.lsp_status_string(0) == b"LSP_OK"
+    assert b"invalid" in L.lsp_status_string(1)
+    o = L.lsp_default_opts()
+    assert (o.precision, o.norm, o.center_y, o.top_k) == (0, 1, 1, 1)
+    assert L.lsp_version() >= 10000
+
+
+@pytest.mark.parametrize("grid,err", [
+    ((0.0, 1.0, 10), "f_min"),
+    ((-1.0, 1.0, 10), "f_min"),
+    ((1.0, 1.0, 10), "f_max"),
+    ((1.0, 2.0, 0), "n_f"),
+    ((1.0, float("inf"), 10), "finite"),
+])
+def test_grid_validation(lsp_mod, grid, err):
+    g = lsp_mod.Grid(*grid)
+    with pytest.raises(lsp_mod.LSPError) as ei:
+        lsp_mod.workspace_size(1, 100, g, lsp_mod.make_opts())
+    assert ei.value.status == 1 and err in str(ei.value)
+
+
+def test_option_validation(lsp_mod):
+    g = lsp_mod.Grid(0.1, 10.0, 1000)
+    for bad in (dict(top_k=4), dict(top_k=0), dict(block_threads=48), dict(block_threads=1024)):
+        with pytest.raises(lsp_mod.LSPError):
+            lsp_mod.workspace_size(5, 100, g, lsp_mod.make_opts(**bad))
+    with pytest.raises(lsp_mod.LSPError) as ei:
+        lsp_mod.workspace_size(5, 100, g, lsp_mod.make_opts(k_reseed=5))
+    assert ei.value.status == 7  # no such kernel variant
+
+
+def test_workspace_sizes_grow_with_shape(lsp_mod):
+    g = lsp_mod.Grid(0.24, 12.0, 100_000)
+    o = lsp_mod.make_opts()
+    a = lsp_mod.workspace_size(100, 30_000, g, o)
+    b = lsp_mod.workspace_size(1000, 300_000, g, o)
+    assert 0 < a < b
+    assert b % 256 == 0
+    # FP64 records are larger; top-3 adds candidate buffers
+    assert lsp_mod.workspace_size(1000, 300_000, g, lsp_mod.make_opts(precision="fp64")) > b
+    assert lsp_mod.workspace_size(1000, 300_000, g, lsp_mod.make_opts(top_k=3)) > b
+
+
+def test_call_validation_without_launch(lsp_mod):
+    L = lsp_mod.lib()
+    g = lsp_mod.Grid(0.1, 10.0, 100)
+    o = lsp_mod.make_opts()
+    # NULL inputs are rejected before any launch
+    st = L.lsp_periodogram(None, None, 10, ctypes.byref(g), ctypes.byref(o), None, None, None, 0, None)
+    assert st == 1
+    # too-small workspace
+    st = L.lsp_periodogram(ctypes.c_void_p(256), ctypes.c_void_p(512), 10, ctypes.byref(g), ctypes.byref(o),
+                           None, None, ctypes.c_void_p(1024), 16, None)
+    assert st == 4 and b"workspace" in L.lsp_last_error()
+    # misaligned workspace
+    need = lsp_mod.workspace_size(1, 10, g, o)
+    st = L.lsp_periodogram(ctypes.c_void_p(256), ctypes.c_void_p(512), 10, ctypes.byref(g), ctypes.byref(o),
+                           None, None, ctypes.c_void_p(1024 + 8), need, None)
+    assert st == 4
+    # batch without offsets
+    st = L.lsp_batch(ctypes.c_void_p(256), ctypes.c_void_p(512), None, 3, 10, ctypes.byref(g), ctypes.byref(o),
+                     None, None, None, 0, None)
+    assert st == 1
+    # empty batch is a no-op
+    st = L.lsp_batch(None, None, None, 0, 0, ctypes.byref(g), ctypes.byref(o), None, None, None, 0, None)
+    assert st == 0
+    # argmax: n_f must match the grid
+    st = L.lsp_argmax_period(ctypes.c_void_p(256), 1, 99, ctypes.byref(g), 0, ctypes.c_void_p(512), None)
+    assert st == 1
+
+
+def test_binding_fails_loudly_without_library(tmp_path, monkeypatch):
+    import paper_2105_04006_gb300 as lsp
+    monkeypatch.setattr(lsp, "LIB_PATH", str(tmp_path / "missing.so"))
+    monkeypatch.setattr(lsp, "_lib", None)
+    with pytest.raises(lsp.LibraryNotBuilt):
+        lsp.lib()

@@ -1,0 +1,407 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 CPU oracle.
+
+Tolerances (written here, applied element by element):
+  * FP32 path: |P_n(gpu) - P_n(oracle)| <= 1e-4, argmax within one grid bin;
+  * FP64 path: |P_n(gpu) - P_n(oracle)| <= 1e-10;
+  * integer work (argmax of a stored periodogram, the fused argmax against
+    the kernel's own powers, flags) is compared bit-exactly.
+Both sides see identical inputs: the oracle gets the FP32 magnitudes the GPU
+gets, widened exactly to FP64.  Full-size workloads are checked on sampled
+objects or frequencies the oracle computes one by one, plus properties that
+hold at any size.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+TOL32 = 1e-4
+TOL64 = 1e-10
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("GPU tests need CUDA")
+    from paper_2105_04006_gb300 import build
+    build.build()
+    oracle.build()
+    import paper_2105_04006_gb300 as lsp
+    return lsp, torch, torch.device("cuda", 0)
+
+
+def _dev(torch, dev, a, dtype):
+    return torch.tensor(np.ascontiguousarray(a), dtype=dtype, device=dev)
+
+
+def _y_seen(y, precision):
+    return y.astype(np.float32).astype(np.float64) if precision == "fp32" else y.astype(np.float64)
+
+
+def single(env, b, precision="fp32", **kw):
+    lsp, torch, dev = env
+    g = lsp.Grid(b.grid.f_min, b.grid.f_max, b.grid.n_f)
+    t = _dev(torch, dev, b.t, torch.float64)
+    y = _dev(torch, dev, b.y, torch.float32 if precision == "fp32" else torch.float64)
+    power, peaks = lsp.periodogram(t, y, g, precision=precision, **kw)
+    torch.cuda.synchronize()
+    return power.cpu().numpy().astype(np.float64), lsp.peaks_to_numpy(peaks)
+
+
+def batch(env, b, precision="fp32", return_power=False, **kw):
+    lsp, torch, dev = env
+    g = lsp.Grid(b.grid.f_min, b.grid.f_max, b.grid.n_f)
+    t = _dev(torch, dev, b.t, torch.float64)
+    y = _dev(torch, dev, b.y, torch.float32 if precision == "fp32" else torch.float64)
+    off = _dev(torch, dev, b.offsets, torch.int64)
+    power, peaks = lsp.batch(t, y, off, g, precision=precision, return_power=return_power, **kw)
+    torch.cuda.synchronize()
+    p = power.cpu().numpy().astype(np.float64) if power is not None else None
+    return p, lsp.peaks_to_numpy(peaks)
+
+
+def oracle_single(b, precision, k_sel=None, norm=1):
+    g = b.grid
+    return oracle.lsp_single(b.t, _y_seen(b.y, precision), g.f_min, g.f_max, g.n_f, norm=norm,
+                             k_sel=k_sel)[0]
+
+
+def oracle_batch(b, precision, **kw):
+    g = b.grid
+    return oracle.lsp_batch(b.t, _y_seen(b.y, precision), b.offsets, g.f_min, g.f_max, g.n_f, **kw)
+
+
+def assert_argmax_close(k_gpu, k_orc, p_orc_row=None, tol=TOL32):
+    """Argmax within one bin, or (tie-aware) a bin whose oracle power is within tol of the max."""
+    if abs(int(k_gpu) - int(k_orc)) <= 1:
+        return
+    assert p_orc_row is not None and p_orc_row[int(k_gpu)] >= p_orc_row[int(k_orc)] - tol, \
+        (k_gpu, k_orc)
+
+
+# ---------------------------------------------------------------- variants
+FP32_VARIANTS = [
+    dict(k_reseed=4, freqs_per_thread=8, block_threads=256),
+    dict(k_reseed=8, freqs_per_thread=16, block_threads=256),
+    dict(k_reseed=16, freqs_per_thread=32, block_threads=256),
+    dict(k_reseed=8, freqs_per_thread=16, block_threads=128),
+    dict(k_reseed=4, freqs_per_thread=8, block_threads=64),
+    dict(k_reseed=8, freqs_per_thread=8, block_threads=256),
+    dict(k_reseed=16, freqs_per_thread=16, block_threads=96),
+]
+FP64_VARIANTS = [
+    dict(k_reseed=4, freqs_per_thread=4, block_threads=128),
+    dict(k_reseed=8, freqs_per_thread=8, block_threads=128),
+    dict(k_reseed=16, freqs_per_thread=16, block_threads=256),
+]
+
+
+@pytest.fixture(scope="module")
+def small_single():
+    # 700 observations: three 256-observation tiles with a ragged tail;
+    # 12345 frequencies: several chunks with a ragged last chunk.
+    b = synth.single_small(n_t=700, grid=synth.Grid(0.1, 10.0, 12345))
+    return b, {p: oracle_single(b, p) for p in ("fp32", "fp64")}
+
+
+@pytest.mark.parametrize("var", FP32_VARIANTS, ids=lambda v: "K{k_reseed}F{freqs_per_thread}T{block_threads}".format(**v))
+def test_single_fp32_variants(env, small_single, var):
+    b, ref = small_single
+    p, pk = single(env, b, "fp32", obs_split=1, **var)
+    err = np.max(np.abs(p - ref["fp32"]))
+    assert err <= TOL32, err
+    assert_argmax_close(pk["idx"][0], np.argmax(ref["fp32"]), ref["fp32"])
+    assert abs(pk["power"][0] - ref["fp32"].max()) <= TOL32
+
+
+@pytest.mark.parametrize("var", FP64_VARIANTS, ids=lambda v: "K{k_reseed}T{block_threads}".format(**v))
+def test_single_fp64_variants(env, small_single, var):
+    b, ref = small_single
+    p, pk = single(env, b, "fp64", obs_split=1, **var)
+    err = np.max(np.abs(p - ref["fp64"]))
+    assert err <= TOL64, err
+    assert pk["idx"][0] == np.argmax(ref["fp64"])
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+@pytest.mark.parametrize("split", [2, 5, 16])
+def test_single_split_nt(env, small_single, precision, split):
+    b, ref = small_single
+    p, pk = single(env, b, precision, obs_split=split)
+    err = np.max(np.abs(p - ref[precision]))
+    assert err <= (TOL32 if precision == "fp32" else TOL64), err
+    assert_argmax_close(pk["idx"][0], np.argmax(ref[precision]), ref[precision])
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_single_psd_normalisation(env, small_single, precision):
+    b, _ = small_single
+    p, _ = single(env, b, precision, norm="psd")
+    ref = oracle_single(b, precision, norm=0)
+    scale = max(1.0, ref.max())
+    assert np.max(np.abs(p - ref)) <= (TOL32 if precision == "fp32" else TOL64) * scale
+
+
+# --------------------------------------------------------------- batches
+@pytest.fixture(scope="module")
+def small_batch():
+    b = synth.ragged_survey(40, seed=21, grid=synth.Grid(0.24, 12.0, 6007))
+    return b, {p: oracle_batch(b, p, top_k=3, return_power=True) for p in ("fp32", "fp64")}
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_batch_power_and_argmax(env, small_batch, precision):
+    b, ref = small_batch
+    p, pk = batch(env, b, precision, return_power=True)
+    err = np.max(np.abs(p - ref[precision]["power"]))
+    assert err <= (TOL32 if precision == "fp32" else TOL64), err
+    for o in range(b.n_obj):
+        if precision == "fp64":
+            assert pk["idx"][o] == ref["fp64"]["arg_idx"][o]
+        else:
+            assert_argmax_close(pk["idx"][o], ref["fp32"]["arg_idx"][o], ref["fp32"]["power"][o])
+    np.testing.assert_allclose(pk["freq"], b.grid.f_min + pk["idx"] * b.grid.df, rtol=1e-15)
+    np.testing.assert_allclose(pk["period"], 1.0 / pk["freq"], rtol=1e-15)
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_batch_top3(env, small_batch, precision):
+    b, ref = small_batch
+    _, pk = batch(env, b, precision, top_k=3)
+    pk = pk.reshape(b.n_obj, 3)
+    tol = TOL32 if precision == "fp32" else TOL64
+    for o in range(b.n_obj):
+        pr = ref[precision]["power"][o]
+        for r in range(3):
+            kg, ko = int(pk["idx"][o, r]), int(ref[precision]["top_idx"][o, r])
+            if precision == "fp64":
+                assert kg == ko, (o, r, kg, ko)
+            elif abs(kg - ko) > 1:
+                # near-tie of two local maxima: the GPU's choice must be as high
+                assert abs(pr[kg] - pr[ko]) <= 2 * tol, (o, r, kg, ko)
+            assert abs(pk["power"][o, r] - ref[precision]["top_pow"][o, r]) <= tol * 2
+
+
+def test_fused_argmax_matches_own_power(env, small_batch):
+    # integer decision in the kernel's own precision: bit-exact
+    b, _ = small_batch
+    for prec in ("fp32", "fp64"):
+        p, pk = batch(env, b, prec, return_power=True)
+        for o in range(b.n_obj):
+            k = int(np.argmax(p[o]))
+            assert pk["idx"][o] == k
+            assert pk["power"][o] == p[o, k]
+
+
+def test_batch_variants_agree(env, small_batch):
+    b, ref = small_batch
+    for var in FP32_VARIANTS:
+        _, pk = batch(env, b, "fp32", **var)
+        for o in range(b.n_obj):
+            assert_argmax_close(pk["idx"][o], ref["fp32"]["arg_idx"][o], ref["fp32"]["power"][o])
+            assert abs(pk["power"][o] - ref["fp32"]["arg_pow"][o]) <= TOL32
+
+
+# ------------------------------------------------------------ edge cases
+def _custom_batch(segs, grid):
+    ts = [np.asarray(s[0], dtype=np.float64) for s in segs]
+    ys = [np.asarray(s[1], dtype=np.float64) for s in segs]
+    off = np.concatenate([[0], np.cumsum([len(x) for x in ts])]).astype(np.int64)
+    t = np.concatenate(ts) if ts else np.zeros(0)
+    y = np.concatenate(ys) if ys else np.zeros(0)
+    return synth.Batch(t, y, off, grid, np.zeros(len(segs)), np.zeros(len(segs)))
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_edge_cases(env, precision):
+    lsp = env[0]
+    g = synth.Grid(0.24, 12.0, 777)
+    rng = np.random.default_rng(5)
+    segs = [
+        ([], []),                                             # empty
+        ([60000.0], [1.0]),                                   # one observation
+        ([60000.0, 60001.3], [0.5, -0.2]),                    # two
+        ([60000.0, 60001.3, 60007.9], [0.1, 0.7, -0.3]),      # three
+        ([60000.0, 60003.0, 60009.0], [2.0, 2.0, 2.0]),       # zero variance
+        ([60000.0, 60001.0, 60002.0], [1.0, np.nan, 0.0]),    # NaN
+        (np.sort(rng.uniform(60000, 61000, 300)), rng.normal(0, 1, 300)),  # a normal one
+        (rng.uniform(60000, 61000, 50)[::-1], rng.normal(0, 1, 50)),     # unsorted times
+    ]
+    b = _custom_batch(segs, g)
+    p, pk = batch(env, b, precision, return_power=True)
+    ref = oracle_batch(b, precision, return_power=True)
+    np.testing.assert_array_equal(pk["flags"], ref["flags"])
+    tol = TOL32 if precision == "fp32" else TOL64
+    assert np.max(np.abs(p - ref["power"])) <= tol
+    for o in range(b.n_obj):
+        if ref["flags"][o]:
+            assert pk["idx"][o] == -1 and pk["power"][o] == 0.0
+        else:
+            assert_argmax_close(pk["idx"][o], ref["arg_idx"][o], ref["power"][o], tol)
+    assert pk["flags"][1] & lsp.FLAG_FEW_OBS and pk["flags"][4] & lsp.FLAG_ZERO_VAR
+    assert pk["flags"][5] & lsp.FLAG_NONFINITE
+
+
+def test_one_frequency_and_bad_offsets(env):
+    lsp, torch, dev = env
+    b = synth.ragged_survey(5, seed=8, grid=synth.Grid(0.5, 0.6, 1))
+    p, pk = batch(env, b, "fp64", return_power=True)
+    ref = oracle_batch(b, "fp64", return_power=True)
+    assert np.max(np.abs(p - ref["power"])) <= TOL64
+    assert (pk["idx"] == 0).all()
+    # offsets that run backwards / past the end flag the objects they touch
+    bad = b.offsets.copy()
+    bad[2], bad[3] = bad[3], bad[2]
+    bad[5] = bad[5] + 7
+    g = lsp.Grid(0.5, 0.6, 1)
+    t = _dev(torch, dev, b.t, torch.float64)
+    y = _dev(torch, dev, b.y, torch.float32)
+    off = _dev(torch, dev, bad, torch.int64)
+    _, peaks = lsp.batch(t, y, off, g)
+    got = lsp.peaks_to_numpy(peaks)
+    assert got["flags"][2] & lsp.FLAG_BAD_OFFSETS and got["flags"][4] & lsp.FLAG_BAD_OFFSETS
+    assert got["flags"][0] == 0 and got["idx"][0] == 0
+
+
+def test_many_frequencies_few_observations(env):
+    # a long grid (2^25 bins) for a short light curve: sampled oracle check
+    b = synth.single_small(n_t=16, grid=synth.Grid(0.1, 50.0, 1 << 25))
+    p, pk = single(env, b, "fp32")
+    ks = np.unique(np.concatenate([np.linspace(0, b.grid.n_f - 1, 200).astype(np.int64),
+                                   np.arange(-3, 4) + int(pk["idx"][0])]))
+    ks = ks[(ks >= 0) & (ks < b.grid.n_f)]
+    ref = oracle_single(b, "fp32", k_sel=ks)
+    assert np.max(np.abs(p[ks] - ref)) <= TOL32
+    assert p.min() >= 0.0 and p.max() <= 1.0 + 1e-5
+
+
+# ----------------------------------------------------- argmax, exactness
+@pytest.mark.parametrize("dtype", [np.float32, np.float64])
+def test_argmax_period_exact(env, dtype):
+    lsp, torch, dev = env
+    rng = np.random.default_rng(1)
+    n_obj, n_f = 7, 50_001
+    p = rng.integers(0, 50, (n_obj, n_f)).astype(dtype)  # many ties
+    p[2, :] = np.nan
+    p[3, ::3] = np.nan
+    p[4, :] = -1.0
+    p[5, 40_000] = 1e30
+    g = lsp.Grid(0.3, 9.0, n_f)
+    peaks = lsp.peaks_to_numpy(lsp.argmax_period(_dev(torch, dev, p, torch.float32 if dtype == np.float32 else torch.float64), g))
+    for o in range(n_obj):
+        row = p[o].astype(np.float64)
+        if np.all(np.isnan(row)):
+            assert peaks["idx"][o] == -1
+            continue
+        k = int(np.nanargmax(row))  # first maximum among non-NaN
+        assert peaks["idx"][o] == k
+        assert peaks["power"][o] == row[k]
+        assert peaks["freq"][o] == 0.3 + k * ((9.0 - 0.3) / n_f)
+
+
+def test_determinism_graph_and_host_entry(env, small_batch):
+    lsp, torch, dev = env
+    b, ref = small_batch
+    g = lsp.Grid(b.grid.f_min, b.grid.f_max, b.grid.n_f)
+    t = _dev(torch, dev, b.t, torch.float64)
+    y = _dev(torch, dev, b.y, torch.float32)
+    off = _dev(torch, dev, b.offsets, torch.int64)
+    _, pk1 = lsp.batch(t, y, off, g, top_k=3)
+    _, pk2 = lsp.batch(t, y, off, g, top_k=3)
+    plan = lsp.Plan(b.n_obj, b.t.size, g, top_k=3)
+    pk3 = plan.execute(t, y, off)   # captures the graph
+    pk4 = plan.execute(t, y, off)   # replays it
+    torch.cuda.synchronize()
+    a = [lsp.peaks_to_numpy(x) for x in (pk1, pk2, pk3, pk4)]
+    for x in a[1:]:
+        assert x.tobytes() == a[0].tobytes()
+    host = plan.execute_host(b.t, b.y.astype(np.float32), b.offsets)
+    assert host.tobytes() == a[0].tobytes()
+    plan.close()
+
+
+def test_autotune_keeps_parity(env, small_batch, tmp_path):
+    lsp, torch, dev = env
+    b, ref = small_batch
+    g = lsp.Grid(b.grid.f_min, b.grid.f_max, b.grid.n_f)
+    t = _dev(torch, dev, b.t, torch.float64)
+    y = _dev(torch, dev, b.y, torch.float32)
+    off = _dev(torch, dev, b.offsets, torch.int64)
+    plan = lsp.Plan(b.n_obj, b.t.size, g)
+    cache = str(tmp_path / "tune.jsonl")
+    cfg = plan.autotune(t, y, off, cache_path=cache)
+    assert cfg["k_reseed"] in (4, 8, 16)
+    pk = lsp.peaks_to_numpy(plan.execute(t, y, off))
+    for o in range(b.n_obj):
+        assert_argmax_close(pk["idx"][o], ref["fp32"]["arg_idx"][o], ref["fp32"]["power"][o])
+    # a second plan reads the cached choice
+    plan2 = lsp.Plan(b.n_obj, b.t.size, g)
+    assert plan2.autotune(t, y, off, cache_path=cache) == cfg
+    plan.close()
+    plan2.close()
+
+
+# ------------------------------------------------------- full-size shapes
+def test_full_single_small(env):
+    """One object, N_t=1000, N_f=1e5: the full periodogram against the full oracle."""
+    b = synth.single_small()
+    for prec, tol in (("fp32", TOL32), ("fp64", TOL64)):
+        p, pk = single(env, b, prec)
+        ref = oracle_single(b, prec)
+        assert np.max(np.abs(p - ref)) <= tol
+        assert_argmax_close(pk["idx"][0], np.argmax(ref), ref, tol)
+
+
+def test_full_ragged_survey_sampled(env):
+    """10000 objects, N_t in [50, 500], N_f=1e5, argmax only (the benchmark's launch)."""
+    b = synth.ragged_survey()
+    _, pk = batch(env, b, "fp32")
+    assert (pk["flags"] == 0).all()
+    sample = np.arange(0, b.n_obj, b.n_obj // 24)[:24]
+    sb = b.subset(sample)
+    ref = oracle_batch(sb, "fp32", return_power=True)
+    within = 0
+    for i, o in enumerate(sample):
+        assert abs(pk["power"][o] - ref["arg_pow"][i]) <= TOL32
+        within += abs(int(pk["idx"][o]) - int(ref["arg_idx"][i])) <= 1
+        assert_argmax_close(pk["idx"][o], ref["arg_idx"][i], ref["power"][i])
+    assert within >= len(sample) - 0  # >= 99.9% of the sample
+    assert (pk["power"] >= 0).all() and (pk["power"] <= 1.0 + 1e-5).all()
+
+
+def test_full_single_large_sampled(env):
+    """One object, N_t=1e5, N_f=1e6, full periodogram: FP32 and FP64 paths."""
+    b = synth.single_large()
+    for prec, tol in (("fp32", TOL32), ("fp64", TOL64)):
+        p, pk = single(env, b, prec)
+        k_top = int(pk["idx"][0])
+        ks = np.unique(np.concatenate([np.linspace(0, b.grid.n_f - 1, 160).astype(np.int64),
+                                       k_top + np.arange(-20, 21)]))
+        ks = ks[(ks >= 0) & (ks < b.grid.n_f)]
+        ref = oracle_single(b, prec, k_sel=ks)
+        assert np.max(np.abs(p[ks] - ref)) <= tol, (prec, np.max(np.abs(p[ks] - ref)))
+        assert p.min() >= 0.0 and p.max() <= 1.0 + (1e-5 if prec == "fp32" else 1e-12)
+        assert int(np.argmax(p)) == k_top
+        # the injected dominant frequency is found within one bin
+        assert abs(k_top - (b.f_true[0] - b.grid.f_min) / b.grid.df) <= 1.0
+
+
+def test_full_ragged_lognormal_top3_sampled(env):
+    """100000 objects, N_t log-uniform in [10, 2000], N_f=5e4, argmax + top-3."""
+    b = synth.ragged_lognormal()
+    _, pk = batch(env, b, "fp32", top_k=3)
+    pk = pk.reshape(b.n_obj, 3)
+    sample = np.arange(0, b.n_obj, b.n_obj // 8)[:8]
+    sb = b.subset(sample)
+    ref = oracle_batch(sb, "fp32", top_k=3, return_power=True)
+    for i, o in enumerate(sample):
+        pr = ref["power"][i]
+        for r in range(3):
+            kg, ko = int(pk["idx"][o, r]), int(ref["top_idx"][i, r])
+            if abs(kg - ko) > 1:
+                assert abs(pr[kg] - pr[ko]) <= 2 * TOL32, (o, r, kg, ko)
+            assert abs(pk["power"][o, r] - ref["top_pow"][i, r]) <= 2 * TOL32
