@@ -236,11 +236,12 @@ lsp_status run(const Layout& L, const double* t, const void* y, const int64_t* o
   ml.n_chunks = L.n_chunks;
   ml.split = L.split;
   ml.n_items = L.n_items;
-  if (ev_main0) LSP_CUDA(cudaEventRecord(ev_main0, st), "timing event");
+  // External records become event-record nodes when captured into a graph.
+  if (ev_main0) LSP_CUDA(cudaEventRecordWithFlags(ev_main0, st, cudaEventRecordExternal), "timing event");
   LSP_CUDA(launch_main(ml, st), "main kernel");
-  if (ev_main1) LSP_CUDA(cudaEventRecord(ev_main1, st), "timing event");
+  if (ev_main1) LSP_CUDA(cudaEventRecordWithFlags(ev_main1, st, cudaEventRecordExternal), "timing event");
   if (L.split > 1)
-    LSP_CUDA(launch_combine(L.prec, part, L.split, L.n_f, obj, power_out, best, cand, st),
+    LSP_CUDA(launch_combine(L.prec, part, L.split, L.n_f, obj, rec, power_out, best, cand, st),
              "split combine");
   if (peaks)
     LSP_CUDA(launch_finalize(obj, best, cand, L.n_obj, L.n_res_chunks, L.top_k, L.f_min, L.df,

@@ -165,9 +165,79 @@ __device__ __forceinline__ Real lsp_power(Real xc, Real xs, Real cc, Real cs, Re
   return Real(0.5) * p;
 }
 
+// The FP32 sums determine Eq. 2's smaller denominator, (N - R)/2, only to
+// about 1e-6 N absolute (phase and rounding errors of N unit terms), so the
+// power's relative error grows like 1e-6 N / (N - R).  Where (N - R) falls
+// below this fraction of N (all doubled phases nearly aligned, e.g. a daily
+// alias of a narrow nightly window, or N_t of 2-3), the FP32 kernels
+// re-evaluate the bin in FP64 (exact_power_warp).
+constexpr float kIllConditioned = 0.05f;
+
+__device__ __forceinline__ bool ill_conditioned_f32(float cc, float cs, float n) {
+  const float c2 = 2.0f * cc - n, s2 = 2.0f * cs;
+  const float r = sqrtf(c2 * c2 + s2 * s2);
+  return n - r < kIllConditioned * n;
+}
+
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+  return v;
+}
+
+// Power at frequency k from FP64 sums over the object's records, evaluated by
+// the whole warp (lanes stride the observations).  Phases are exact:
+// frac(a + k b) from the 64-bit fixed-point record words.  Every lane returns
+// the same value.  Must be called by all 32 lanes.
+static __device__ __noinline__ double exact_power_warp(const RecF32* __restrict__ rec, int64_t begin, int n,
+                                                uint32_t k, double norm_scale);
+
 template <typename Real> struct EpsRel;
 template <> struct EpsRel<float> { static constexpr float v = 1e-6f; };
 template <> struct EpsRel<double> { static constexpr double v = 1e-12; };
+
+static __device__ __noinline__ double exact_power_warp(const RecF32* __restrict__ rec, int64_t begin, int n,
+                                                uint32_t k, double norm_scale) {
+  double xc = 0.0, xs = 0.0, cc = 0.0, cs = 0.0;
+  for (int j = threadIdx.x & 31; j < n; j += 32) {
+    const RecF32 r = rec[begin + j];
+    const uint64_t a = ((uint64_t)r.a_hi << 32) | r.a_lo;
+    const uint64_t b = ((uint64_t)r.b_hi << 32) | r.b_lo;
+    double c, s;
+    seed_sincos_f64(a + (uint64_t)k * b, c, s);
+    const double y = (double)r.y;
+    xc = fma(y, c, xc);
+    xs = fma(y, s, xs);
+    cc = fma(c, c, cc);
+    cs = fma(c, s, cs);
+  }
+  xc = warp_sum_d(xc);
+  xs = warp_sum_d(xs);
+  cc = warp_sum_d(cc);
+  cs = warp_sum_d(cs);
+  return norm_scale * lsp_power<double>(xc, xs, cc, cs, (double)n, EpsRel<double>::v);
+}
+
+// Replace the ill-conditioned bins (bit m of `bad`: bin k0 + m) of every lane
+// of the warp by their FP64 re-evaluation.  Called by all 32 lanes.
+template <int F>
+__device__ __forceinline__ void fix_ill_conditioned(float (&pv)[F], uint32_t bad, uint32_t k0,
+                                                    const RecF32* __restrict__ rec, int64_t begin,
+                                                    int n, double norm_scale) {
+  if (!__any_sync(0xffffffffu, bad != 0u)) return;
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int m = 0; m < F; ++m) {
+    unsigned mask = __ballot_sync(0xffffffffu, (bad >> m) & 1u);
+    while (mask) {
+      const int l = __ffs(mask) - 1;
+      mask &= mask - 1;
+      const uint32_t k = __shfl_sync(0xffffffffu, k0 + (uint32_t)m, l);
+      const double p = exact_power_warp(rec, begin, n, k, norm_scale);
+      if (lane == l) pv[m] = (float)p;
+    }
+  }
+}
 
 // ------------------------------------------------------ chunk reductions
 // (p, k) pair ordering: higher power first, lower index on ties.

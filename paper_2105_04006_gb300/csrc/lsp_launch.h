@@ -56,7 +56,8 @@ size_t main_dyn_smem(int prec, int fpt, int threads, int top);
 constexpr int kCombineThreads = 256;
 constexpr int kCombinePerThread = 4;
 cudaError_t launch_combine(int prec, const void* part, int split, int64_t n_f, const ObjInfo* obj,
-                           void* power_out, ChunkBest* best, ChunkCand* cand, cudaStream_t stream);
+                           const void* rec, void* power_out, ChunkBest* best, ChunkCand* cand,
+                           cudaStream_t stream);
 
 // Per-object peaks from the chunk results.
 cudaError_t launch_finalize(const ObjInfo* obj, const ChunkBest* best, const ChunkCand* cand,

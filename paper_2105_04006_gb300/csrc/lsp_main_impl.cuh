@@ -158,6 +158,7 @@ __global__ void __launch_bounds__(256) main_f32_packed(MainParams<RecF32, float>
     if (p.split == 1) {
       float pv[F];
       const float nf = (float)oi.n, scale = (float)oi.norm_scale;
+      uint32_t bad = 0u;
 #pragma unroll
       for (int m = 0; m < K; ++m) {
         float a0, a1, b0, b1, c0, c1, d0, d1;
@@ -167,7 +168,11 @@ __global__ void __launch_bounds__(256) main_f32_packed(MainParams<RecF32, float>
         f2_unpack(cs[m], d0, d1);
         pv[m] = scale * lsp_power<float>(a0, b0, c0, d0, nf, EpsRel<float>::v);
         pv[K + m] = scale * lsp_power<float>(a1, b1, c1, d1, nf, EpsRel<float>::v);
+        if (ill_conditioned_f32(c0, d0, nf) && (int64_t)k0 + m < p.n_f) bad |= 1u << m;
+        if (ill_conditioned_f32(c1, d1, nf) && (int64_t)k1 + m < p.n_f) bad |= 1u << (K + m);
       }
+      if (oi.flags) bad = 0u;
+      fix_ill_conditioned<F>(pv, bad, k0, p.rec, oi.begin, oi.n, oi.norm_scale);
       if (p.power_out) store_row<F>(p.power_out + it.o * p.n_f, (int64_t)k0, pv, p.n_f);
       const int64_t res = it.o * p.n_chunks + it.chunk;
       chunk_results<float, F>(pv, (int64_t)k0, kc0, p.n_f, p.best + res,
@@ -255,9 +260,18 @@ __global__ void __launch_bounds__(256) main_scalar(MainParams<Rec, Real> p) {
     if (p.split == 1) {
       Real pv[F];
       const Real nf = (Real)oi.n, scale = (Real)oi.norm_scale;
+      uint32_t bad = 0u;
 #pragma unroll
-      for (int m = 0; m < K; ++m)
+      for (int m = 0; m < K; ++m) {
         pv[m] = scale * lsp_power<Real>(xc[m], xs[m], cc[m], cs[m], nf, EpsRel<Real>::v);
+        if constexpr (std::is_same<Real, float>::value) {
+          if (ill_conditioned_f32(cc[m], cs[m], nf) && (int64_t)k0 + m < p.n_f) bad |= 1u << m;
+        }
+      }
+      if constexpr (std::is_same<Real, float>::value) {
+        if (oi.flags) bad = 0u;
+        fix_ill_conditioned<F>(pv, bad, k0, p.rec, oi.begin, oi.n, oi.norm_scale);
+      }
       if (p.power_out) store_row<F>(p.power_out + it.o * p.n_f, (int64_t)k0, pv, p.n_f);
       const int64_t res = it.o * p.n_chunks + it.chunk;
       chunk_results<Real, F>(pv, (int64_t)k0, kc0, p.n_f, p.best + res,

@@ -1,5 +1,6 @@
 // lsp_post.cu -- split-N_t combine, per-object peaks, stored-periodogram argmax.
 #include <cmath>
+#include <type_traits>
 
 #include "../../include/lsp.h"
 #include "lsp_launch.h"
@@ -39,7 +40,8 @@ namespace {
 template <typename Real>
 __global__ void __launch_bounds__(kCombineThreads) combine_kernel(
     const Real* __restrict__ part, int split, int64_t n_f, const ObjInfo* __restrict__ obj,
-    Real* __restrict__ power_out, ChunkBest* __restrict__ best, ChunkCand* __restrict__ cand) {
+    const RecF32* __restrict__ rec, Real* __restrict__ power_out, ChunkBest* __restrict__ best,
+    ChunkCand* __restrict__ cand) {
   constexpr int NP = kCombinePerThread;
   extern __shared__ __align__(16) unsigned char dyn_smem[];
   Real* s_pw = reinterpret_cast<Real*>(dyn_smem);
@@ -50,6 +52,7 @@ __global__ void __launch_bounds__(kCombineThreads) combine_kernel(
   const int64_t k0 = kc0 + (int64_t)threadIdx.x * NP;
   const Real nf = (Real)oi.n, scale = (Real)oi.norm_scale;
   Real pv[NP];
+  uint32_t bad = 0u;
 #pragma unroll
   for (int m = 0; m < NP; ++m) {
     const int64_t k = k0 + m;
@@ -64,7 +67,12 @@ __global__ void __launch_bounds__(kCombineThreads) combine_kernel(
       }
     }
     pv[m] = oi.flags ? Real(0) : scale * lsp_power<Real>(xc, xs, cc, cs, nf, EpsRel<Real>::v);
+    if constexpr (std::is_same<Real, float>::value) {
+      if (k < n_f && !oi.flags && ill_conditioned_f32(cc, cs, nf)) bad |= 1u << m;
+    }
   }
+  if constexpr (std::is_same<Real, float>::value)
+    fix_ill_conditioned<NP>(pv, bad, (uint32_t)k0, rec, oi.begin, oi.n, oi.norm_scale);
   if (power_out) {
 #pragma unroll
     for (int m = 0; m < NP; ++m)
@@ -291,16 +299,17 @@ cudaError_t launch_max_abs_diff(const float* a, const double* b, int64_t n, doub
 }
 
 cudaError_t launch_combine(int prec, const void* part, int split, int64_t n_f, const ObjInfo* obj,
-                           void* power_out, ChunkBest* best, ChunkCand* cand, cudaStream_t stream) {
+                           const void* rec, void* power_out, ChunkBest* best, ChunkCand* cand,
+                           cudaStream_t stream) {
   const int64_t per_cta = (int64_t)kCombineThreads * kCombinePerThread;
   const unsigned grid = (unsigned)((n_f + per_cta - 1) / per_cta);
   const size_t dyn = cand ? (size_t)per_cta * (prec ? 8 : 4) : 0;
   if (prec)
     combine_kernel<double><<<grid, kCombineThreads, dyn, stream>>>(
-        (const double*)part, split, n_f, obj, (double*)power_out, best, cand);
+        (const double*)part, split, n_f, obj, nullptr, (double*)power_out, best, cand);
   else
     combine_kernel<float><<<grid, kCombineThreads, dyn, stream>>>(
-        (const float*)part, split, n_f, obj, (float*)power_out, best, cand);
+        (const float*)part, split, n_f, obj, (const RecF32*)rec, (float*)power_out, best, cand);
   return cudaGetLastError();
 }
 

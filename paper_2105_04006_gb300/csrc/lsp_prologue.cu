@@ -108,7 +108,7 @@ __global__ void stats_kernel(const double* __restrict__ t, const YT* __restrict_
   if (threadIdx.x == 0) {
     if (bad > 0.0) flags |= LSP_FLAG_NONFINITE;
     if (n < 2) flags |= LSP_FLAG_FEW_OBS;
-    if (!(flags & LSP_FLAG_NONFINITE) && !(s2 > 0.0)) flags |= LSP_FLAG_ZERO_VAR;
+    if (!(flags & LSP_FLAG_NONFINITE) && n > 0 && !(s2 > 0.0)) flags |= LSP_FLAG_ZERO_VAR;
     ObjInfo oi;
     oi.t0 = n > 0 ? 0.5 * (tmin + tmax) : 0.0;
     oi.ymean = mean;

@@ -246,6 +246,34 @@ def test_edge_cases(env, precision):
     assert pk["flags"][5] & lsp.FLAG_NONFINITE
 
 
+def _nightly_batch(n_obj, seed, grid):
+    # observations inside a one-hour window of each night: near multiples of
+    # 1/2 c/d all doubled phases align and Eq. 2's sin^2 denominator nearly
+    # vanishes (the FP32 kernels re-evaluate those bins in FP64)
+    rng = np.random.default_rng(seed)
+    segs = []
+    for _ in range(n_obj):
+        n = int(rng.integers(20, 400))
+        nights = np.sort(rng.choice(3000, n, replace=False)).astype(np.float64)
+        t = 60000.0 + nights + 0.3 + rng.uniform(0, 1.0 / 24.0, n)
+        y = 0.4 * np.sin(2 * np.pi * rng.uniform(0.3, 5.0) * t) + rng.normal(0, 0.2, n)
+        segs.append((t, y))
+    return _custom_batch(segs, grid)
+
+
+def test_nightly_cadence_ill_conditioned_bins(env):
+    b = _nightly_batch(12, 17, synth.Grid(0.24, 12.0, 20011))
+    p, pk = batch(env, b, "fp32", return_power=True)
+    ref = oracle_batch(b, "fp32", return_power=True)
+    assert np.max(np.abs(p - ref["power"])) <= TOL32
+    for o in range(b.n_obj):
+        assert_argmax_close(pk["idx"][o], ref["arg_idx"][o], ref["power"][o])
+    # the same through the split-N_t single-object path (combine kernel)
+    one = b.subset([int(np.argmax(b.n_t))])
+    p1, _ = single(env, one, "fp32", obs_split=7)
+    assert np.max(np.abs(p1 - oracle_single(one, "fp32"))) <= TOL32
+
+
 def test_one_frequency_and_bad_offsets(env):
     lsp, torch, dev = env
     b = synth.ragged_survey(5, seed=8, grid=synth.Grid(0.5, 0.6, 1))
