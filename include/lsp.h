@@ -148,6 +148,27 @@ lsp_status lsp_batch(const double* t, const void* y, const int64_t* offsets, int
                      lsp_stream_t stream);
 
 /*
+ * lsp_batch without a caller workspace, for callers that cannot allocate
+ * device memory (a real-time pipeline whose device-memory budget is fixed at
+ * start-up, a plugin whose host framework has reserved the device memory for
+ * its own pool, a C caller without a device allocator).  The paper has no
+ * counterpart: this is a deployment convenience of this library.
+ * Arguments and results are those of lsp_batch; the scratch memory is a
+ * fixed device array of LSP_NOALLOC_SCRATCH_BYTES inside the library, which
+ * every GPU that loads the library holds until the process exits.  A shape
+ * whose lsp_workspace_size exceeds it returns LSP_E_WORKSPACE, launching
+ * nothing.  The call allocates nothing.  All calls share that one array:
+ * calls that overlap on the GPU (different streams or unordered host
+ * threads) race on it, so order them.  Each call clears what must start at
+ * zero.  The first call on a device looks up the array's address with that
+ * device current; make it outside any stream capture.
+ */
+#define LSP_NOALLOC_SCRATCH_BYTES (32u << 20)
+lsp_status lsp_batch_noalloc(const double* t, const void* y, const int64_t* offsets, int64_t n_obj,
+                             int64_t total_nt, const lsp_grid* grid, const lsp_opts* opts,
+                             void* power_out, lsp_peak* peaks, lsp_stream_t stream);
+
+/*
  * Period of stored periodograms (Section 3.3's separate argmax step):
  * power is n_obj x n_f of type float (LSP_FP32) or double (LSP_FP64); each
  * row's first maximum is written to peaks[o] (idx, power, freq, period;

@@ -77,6 +77,7 @@ EXPORTS = [
     "lsp_periodogram", "lsp_batch", "lsp_argmax_period", "lsp_plan_create", "lsp_plan_execute",
     "lsp_plan_execute_host", "lsp_plan_autotune", "lsp_plan_get_config", "lsp_plan_set_config",
     "lsp_plan_destroy", "lsp_plan_enable_timing", "lsp_plan_main_kernel_ms", "lsp_plan_kernel_count",
+    "lsp_batch_noalloc",
 ]
 
 
@@ -101,6 +102,7 @@ def lib():
             L.lsp_periodogram.argtypes = [P, P, i64, GP, OP, P, P, P, sz, P]
             L.lsp_batch.argtypes = [P, P, P, i64, i64, GP, OP, P, P, P, sz, P]
             L.lsp_argmax_period.argtypes = [P, i64, i64, GP, i32, P, P]
+            L.lsp_batch_noalloc.argtypes = [P, P, P, i64, i64, GP, OP, P, P, P]
             L.lsp_plan_create.argtypes = [ctypes.POINTER(P), i64, i64, GP, OP]
             L.lsp_plan_execute.argtypes = [P, P, P, P, P, P, P]
             L.lsp_plan_execute_host.argtypes = [P, P, P, P, P, P, P]

@@ -265,6 +265,11 @@ lsp_status check_io(int64_t n, const double* t, const void* y) {
 
 }  // namespace
 
+namespace lsp {
+// Lets other translation units of the library report through lsp_last_error.
+void set_last_error(const char* msg) { g_err = msg ? msg : ""; }
+}  // namespace lsp
+
 // ======================================================================= C ABI
 extern "C" {
 
