@@ -58,9 +58,10 @@ def dist_env():
             int(os.environ.get("LOCAL_RANK", 0)))
 
 
-def make_workload(name, rank):
+def make_workload(name, rank, n_obj=None):
     seed = synth.SEEDS[name] + 1_000_003 * rank
-    return synth.by_name(name, seed=seed)
+    kw = {"n_obj": n_obj} if n_obj else {}
+    return synth.by_name(name, seed=seed, **kw)
 
 
 # ------------------------------------------------------------------ clocks
@@ -152,13 +153,24 @@ def recorded_traffic(workload, src_hash):
 def cpu_baseline(b, n_sample, top_k):
     import oracle
     oracle.build()
-    n_sample = min(n_sample, b.n_obj)
-    if b.n_obj == 1:
-        sub, what = b, "the whole object"
-    else:
-        idx = np.linspace(0, b.n_obj - 1, n_sample).astype(np.int64)
-        sub, what = b.subset(idx), f"{n_sample} objects evenly spaced over the batch"
     g = b.grid
+    if b.n_obj == 1:
+        # one object: an evenly spaced subset of its frequencies (about 4e9 pairs)
+        n_sel = int(min(g.n_f, max(1000, 4e9 // max(1, b.t.size))))
+        ks = np.linspace(0, g.n_f - 1, n_sel).astype(np.int64)
+        t0 = time.perf_counter()
+        oracle.lsp_single(b.t, b.y.astype(np.float32).astype(np.float64), g.f_min, g.f_max, g.n_f, k_sel=ks)
+        dt = time.perf_counter() - t0
+        frac = n_sel / g.n_f
+        pairs = b.t.size * n_sel
+        what = ("the whole object" if n_sel == g.n_f else
+                f"{n_sel} of the object's {g.n_f} frequencies, extrapolated to the whole object")
+        return {"value": frac / dt, "unit": "objects/s", "cores": oracle.num_threads(), "kind": "oracle",
+                "sample": f"{what} ({pairs:.3g} pairs, FP64 two-scan Eq. 1-2), {dt:.1f} s",
+                "pairs_per_s": pairs / dt}
+    n_sample = min(n_sample, b.n_obj)
+    idx = np.linspace(0, b.n_obj - 1, n_sample).astype(np.int64)
+    sub, what = b.subset(idx), f"{n_sample} objects evenly spaced over the batch"
     t0 = time.perf_counter()
     oracle.lsp_batch(sub.t, sub.y.astype(np.float32).astype(np.float64), sub.offsets, g.f_min, g.f_max,
                      g.n_f, top_k=top_k, return_power=False)
@@ -174,14 +186,19 @@ def run_reference(args, w, name):
         return 0
     import oracle
     oracle.build()
-    b = make_workload(name, 0)
+    b = make_workload(name, 0, args.n_obj)
     per = w["ref_per_step"]
     g = b.grid
     steps_t = []
 
     def step(i):
         if b.n_obj == 1:
-            sub = b
+            n_sel = int(min(g.n_f, max(1000, 2e9 // max(1, b.t.size))))
+            ks = np.linspace(0, g.n_f - 1, n_sel).astype(np.int64)
+            t0 = time.perf_counter()
+            oracle.lsp_single(b.t, b.y.astype(np.float32).astype(np.float64), g.f_min, g.f_max, g.n_f,
+                              k_sel=ks)
+            return time.perf_counter() - t0, n_sel / g.n_f
         else:
             lo = (i * per) % max(1, b.n_obj - per)
             sub = b.subset(np.arange(lo, lo + per))
@@ -204,7 +221,8 @@ def run_reference(args, w, name):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": {"workload": name, "shape": w["desc"],
-                                        "sample_per_step": f"{per} objects" if b.n_obj > 1 else "whole object"},
+                                        "sample_per_step": (f"{per} objects" if b.n_obj > 1 else
+                                                            "a frequency subsample of the object, extrapolated")},
         "cpu_baseline": {"value": value, "unit": "objects/s", "cores": oracle.num_threads(), "kind": "oracle",
                          "sample": f"{per if b.n_obj > 1 else 1} objects per step, {args.steps} steps"},
         "e2e": {"value": value, "unit": "objects/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -226,14 +244,17 @@ def run_gpu(args, w, name):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
 
-    b = make_workload(name, rank)
+    b = make_workload(name, rank, args.n_obj)
     g = lsp.Grid(b.grid.f_min, b.grid.f_max, b.grid.n_f)
     t = torch.tensor(b.t, dtype=torch.float64, device=dev)
     y = torch.tensor(b.y.astype(np.float32), device=dev)
     off = torch.tensor(b.offsets, dtype=torch.int64, device=dev) if b.n_obj > 1 else None
     power = torch.empty((b.n_obj, g.n_f), dtype=torch.float32, device=dev) if w["power"] else None
     plan = lsp.Plan(b.n_obj, b.t.size, g, top_k=w["top_k"])
-    if not args.no_tune:
+    if args.config:
+        keys = ("k_reseed", "freqs_per_thread", "block_threads", "obs_split", "packed")
+        plan.set_config(**dict(zip(keys, (int(v) for v in args.config.split(",")))))
+    elif not args.no_tune:
         cache = os.path.join(ROOT, "paper_2105_04006_gb300", "_build", "tune_cache.jsonl")
         plan.autotune(t, y, off, cache_path=cache)
     plan.enable_timing(True)
@@ -349,6 +370,10 @@ def main():
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="ragged_survey")
     ap.add_argument("--no-tune", action="store_true", help="use the default kernel configuration")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
+    ap.add_argument("--config", default=None,
+                    help="force a kernel configuration: k_reseed,freqs_per_thread,block_threads,obs_split,packed")
+    ap.add_argument("--n-obj", type=int, default=None,
+                    help="objects in a batch workload (default: the workload's own count)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

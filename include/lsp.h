@@ -109,6 +109,15 @@ lsp_opts lsp_default_opts(void);
 /* Library version, as major*10000 + minor*100 + patch. */
 int32_t lsp_version(void);
 
+/*
+ * Grid-selection rule of Section 4.3: spacing df = 0.1 / t_span in cycles
+ * per unit time (the paper's 0.2 pi / T_max in angular frequency; t_span is
+ * the observing window, the largest one of a batch) and
+ * n_f = round((f_max - f_min) / df).  Writes *grid = {f_min, f_max, n_f};
+ * LSP_E_ARG for a non-positive span or an empty range.
+ */
+lsp_status lsp_grid_for_span(double f_min, double f_max, double t_span, lsp_grid* grid);
+
 /* ---- one-shot entry points -------------------------------------------- */
 
 /*

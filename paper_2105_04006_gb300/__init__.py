@@ -77,7 +77,7 @@ EXPORTS = [
     "lsp_periodogram", "lsp_batch", "lsp_argmax_period", "lsp_plan_create", "lsp_plan_execute",
     "lsp_plan_execute_host", "lsp_plan_autotune", "lsp_plan_get_config", "lsp_plan_set_config",
     "lsp_plan_destroy", "lsp_plan_enable_timing", "lsp_plan_main_kernel_ms", "lsp_plan_kernel_count",
-    "lsp_batch_noalloc",
+    "lsp_batch_noalloc", "lsp_grid_for_span",
 ]
 
 
@@ -103,6 +103,7 @@ def lib():
             L.lsp_batch.argtypes = [P, P, P, i64, i64, GP, OP, P, P, P, sz, P]
             L.lsp_argmax_period.argtypes = [P, i64, i64, GP, i32, P, P]
             L.lsp_batch_noalloc.argtypes = [P, P, P, i64, i64, GP, OP, P, P, P]
+            L.lsp_grid_for_span.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_double, GP]
             L.lsp_plan_create.argtypes = [ctypes.POINTER(P), i64, i64, GP, OP]
             L.lsp_plan_execute.argtypes = [P, P, P, P, P, P, P]
             L.lsp_plan_execute_host.argtypes = [P, P, P, P, P, P, P]
@@ -168,6 +169,13 @@ def make_opts(precision="fp32", norm="standard", center=True, top_k=1, k_reseed=
 def _dtypes(opts: Opts):
     torch = _torch()
     return torch.float64 if opts.precision == FP64 else torch.float32
+
+
+def grid_for_span(f_min: float, f_max: float, t_span: float) -> Grid:
+    """Section 4.3's grid: df = 0.1 / t_span cycles per unit time, n_f = round(range / df)."""
+    g = Grid()
+    _check(lib().lsp_grid_for_span(float(f_min), float(f_max), float(t_span), ctypes.byref(g)))
+    return g
 
 
 def workspace_size(n_obj, total_nt, grid: Grid, opts: Opts) -> int:

@@ -130,7 +130,8 @@ lsp_status resolve(int64_t n_obj, int64_t total_nt, const lsp_grid* g, const lsp
     } else {
       fpt = o.freqs_per_thread ? o.freqs_per_thread
                                : (main_variant_exists(0, 1, k, 2 * k) ? 2 * k : k);
-      threads = o.block_threads ? o.block_threads : 256;
+      // measured on GB300: 128-thread CTAs for batches, 256 for one object
+      threads = o.block_threads ? o.block_threads : (n_obj > 1 ? 128 : 256);
     }
     packed = (l.prec == LSP_FP32 && fpt == 2 * k) ? 1 : 0;
     split_req = o.obs_split;
@@ -299,6 +300,20 @@ lsp_opts lsp_default_opts(void) {
   o.center_y = 1;
   o.top_k = 1;
   return o;
+}
+
+lsp_status lsp_grid_for_span(double f_min, double f_max, double t_span, lsp_grid* grid) {
+  g_err.clear();
+  if (!grid) return fail(LSP_E_ARG, "grid is NULL");
+  if (!(t_span > 0.0) || !std::isfinite(t_span)) return fail(LSP_E_ARG, "t_span must be > 0");
+  if (!(f_max > f_min)) return fail(LSP_E_ARG, "f_max must be > f_min");
+  const double df = 0.1 / t_span;  // 0.2 pi / T_max rad per unit time, in cycles
+  const double n = std::nearbyint((f_max - f_min) / df);
+  if (n < 1.0 || n > (double)(kMaxNf - 65536)) return fail(LSP_E_ARG, "resulting n_f out of range");
+  grid->f_min = f_min;
+  grid->f_max = f_max;
+  grid->n_f = (int64_t)n;
+  return LSP_OK;
 }
 
 lsp_status lsp_workspace_size(int64_t n_obj, int64_t total_nt, const lsp_grid* grid,

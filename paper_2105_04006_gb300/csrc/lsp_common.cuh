@@ -29,6 +29,8 @@ struct __align__(16) ObjInfo {
   int32_t n;         // N_t (0 for an object with bad offsets)
   int32_t flags;     // LSP_FLAG_*
   double norm_scale; // 2 / sum_y2 (standard normalisation) or 1 (PSD)
+  float norm_scale_f; // the same, rounded to FP32 (the FP32 kernels never touch FP64)
+  int32_t pad[3];
 };
 
 // FP32 path record, 32 bytes.  Phase of frequency k at this observation, in
@@ -353,6 +355,119 @@ __device__ void chunk_results(const Real (&pv)[NP], int64_t k0, int64_t k_chunk0
     *cand_out = out;
   }
   __syncthreads();
+}
+
+// ------------------------------------------- FP32 chunk reductions (keys)
+// In the FP32 kernels a (power, index) pair is one 64-bit key,
+//   key = (bits(P) << 32) | (0xFFFFFFFF - k),
+// whose unsigned order is "higher power, then lower index" for P >= 0 (the
+// kernels' powers are never negative or NaN).  Key 0 means "no bin".  This
+// keeps the FP64 pipe (about 1/64 of the FP32 rate on GB300) out of the
+// epilogue.
+__device__ __forceinline__ unsigned long long pkey(float p, uint32_t k) {
+  return ((unsigned long long)__float_as_uint(p) << 32) | (unsigned long long)(0xFFFFFFFFu - k);
+}
+__device__ __forceinline__ float key_power(unsigned long long key) { return __uint_as_float((uint32_t)(key >> 32)); }
+__device__ __forceinline__ int64_t key_index(unsigned long long key) {
+  return key ? (int64_t)(0xFFFFFFFFu - (uint32_t)key) : -1;
+}
+__device__ __forceinline__ unsigned long long umax64(unsigned long long a, unsigned long long b) {
+  return a > b ? a : b;
+}
+__device__ __forceinline__ unsigned long long warp_max_key(unsigned long long v) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) v = umax64(v, __shfl_xor_sync(0xffffffffu, v, off));
+  return v;
+}
+// Block-wide maximum key, returned to every thread; `red` holds blockDim/32 keys.
+__device__ __forceinline__ unsigned long long block_max_key(unsigned long long v, unsigned long long* red) {
+  v = warp_max_key(v);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  v = lane < nw ? red[lane] : 0ull;
+  v = warp_max_key(v);
+  __syncthreads();
+  return v;
+}
+
+// FP32 counterpart of chunk_results: first maximum and (with cand) the top-3
+// interior local maxima and edge bins of the chunk.  `pw` is a shared buffer
+// of blockDim.x * NP floats (top-k only).
+template <int NP>
+__device__ void chunk_results_f32(const float (&pv)[NP], uint32_t k0, int64_t k_chunk0, int64_t n_f,
+                                  ChunkBest* best_out, ChunkCand* cand_out, float* pw,
+                                  unsigned long long* red) {
+  unsigned long long best = 0ull;
+#pragma unroll
+  for (int m = 0; m < NP; ++m)
+    if ((int64_t)k0 + m < n_f) best = umax64(best, pkey(pv[m], k0 + (uint32_t)m));
+  if (cand_out == nullptr) {
+    best = block_max_key(best, red);
+    if (threadIdx.x == 0) *best_out = ChunkBest{(double)key_power(best), key_index(best)};
+    return;
+  }
+  const int chunk_len = blockDim.x * NP;
+  const int64_t nvalid64 = n_f - k_chunk0;
+  const int nvalid = nvalid64 < chunk_len ? (int)nvalid64 : chunk_len;
+  const int base = threadIdx.x * NP;
+#pragma unroll
+  for (int m = 0; m < NP; ++m) pw[base + m] = pv[m];
+  __syncthreads();
+  unsigned long long t0 = 0ull, t1 = 0ull, t2 = 0ull;  // this thread's top-3 interior maxima
+#pragma unroll
+  for (int m = 0; m < NP; ++m) {
+    const int i = base + m;
+    if (i >= 1 && i <= nvalid - 2) {
+      const float v = pw[i];
+      if (v > pw[i - 1] && v >= pw[i + 1]) {
+        const unsigned long long key = pkey(v, (uint32_t)(k_chunk0 + i));
+        if (key > t0) { t2 = t1; t1 = t0; t0 = key; }
+        else if (key > t1) { t2 = t1; t1 = key; }
+        else if (key > t2) { t2 = key; }
+      }
+    }
+  }
+  ChunkCand out;
+  for (int r = 0; r < 3; ++r) {
+    const unsigned long long w = block_max_key(t0, red);
+    out.p[r] = (double)key_power(w);
+    out.k[r] = key_index(w);
+    if (w && t0 == w) { t0 = t1; t1 = t2; t2 = 0ull; }
+  }
+  best = block_max_key(best, red);
+  if (threadIdx.x == 0) {
+    *best_out = ChunkBest{(double)key_power(best), key_index(best)};
+    out.k_first = k_chunk0;
+    out.nvalid = nvalid;
+    out.pad = 0;
+    out.first[0] = nvalid > 0 ? (double)pw[0] : 0.0;
+    out.first[1] = nvalid > 1 ? (double)pw[1] : 0.0;
+    out.last[0] = nvalid > 0 ? (double)pw[nvalid - 1] : 0.0;
+    out.last[1] = nvalid > 1 ? (double)pw[nvalid - 2] : 0.0;
+    *cand_out = out;
+  }
+  __syncthreads();
+}
+
+// Eq. 2 from the FP32 single-scan sums with the SFU's reciprocal square root
+// and fast division (relative error ~1e-7, far inside the FP32 path's budget).
+// Also reports whether the bin is ill-conditioned (see kIllConditioned).
+__device__ __forceinline__ float lsp_power_f32(float xc, float xs, float cc, float cs, float n, bool& ill) {
+  const float c2 = fmaf(2.0f, cc, -n);
+  const float s2 = 2.0f * cs;
+  const float r2 = fmaf(c2, c2, s2 * s2);
+  const float rinv = r2 > 0.0f ? rsqrtf(r2) : 0.0f;
+  const float r = r2 * rinv;
+  const float z2 = fmaf(xc, xc, xs * xs);
+  const float q = fmaf((xc - xs) * (xc + xs), c2, 2.0f * xc * xs * s2) * rinv;
+  const float d1 = n + r, d2 = n - r;
+  const float eps = EpsRel<float>::v * n;
+  ill = d2 < kIllConditioned * n;
+  float p = 0.0f;
+  if (0.5f * d1 > eps) p += __fdividef(fmaxf(z2 + q, 0.0f), d1);
+  if (0.5f * d2 > eps) p += __fdividef(fmaxf(z2 - q, 0.0f), d2);
+  return 0.5f * p;
 }
 
 }  // namespace lsp

@@ -90,30 +90,78 @@ __device__ __forceinline__ Item decode_item(const P& p, int64_t item) {
 // ------------------------------------------------------------------------
 // FP32, two reseed chains of K frequencies per thread in packed f32x2 lanes:
 // lane 0 covers k0 .. k0+K-1, lane 1 covers k0+K .. k0+2K-1.
+//
+// The shared-memory tile holds the 32-byte records as they are.  Each
+// observation costs every thread two SFU seeds (one per chain) and 2K-1
+// packed recurrence steps.  (Measured alternatives that did not pay on
+// GB300: issuing the next observation's seeds one step ahead, integer
+// bit-building of the seed angle instead of I2F, and deriving the second
+// chain's seed from the first by a K-step rotation.)
+
+__device__ __forceinline__ f2_t f2_of(uint32_t lo, uint32_t hi) {
+  f2_t r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "r"(lo), "r"(hi));
+  return r;
+}
+
+__device__ __forceinline__ void seed_pair(const uint4 w2, uint32_t k0, uint32_t k1, f2_t& c2, f2_t& s2) {
+  float c0, s0, c1, s1;
+  seed_sincos_f32(phase_hi32(w2.x, w2.y, w2.z, k0), c0, s0);
+  seed_sincos_f32(phase_hi32(w2.x, w2.y, w2.z, k1), c1, s1);
+  c2 = f2_pack(c0, c1);
+  s2 = f2_pack(s0, s1);
+}
+
+// K steps of the two packed reseed chains at one observation: accumulate the
+// four sums at the current (cos, sin), then rotate by one grid step.
+template <int K>
+__device__ __forceinline__ void recurrence_steps(f2_t (&xc)[K], f2_t (&xs)[K], f2_t (&cc)[K], f2_t (&cs)[K],
+                                                 f2_t c2, f2_t s2, f2_t y2, f2_t cr2, f2_t sr2, f2_t nsr2) {
+#pragma unroll
+  for (int m = 0; m < K; ++m) {
+    xc[m] = f2_fma(y2, c2, xc[m]);
+    xs[m] = f2_fma(y2, s2, xs[m]);
+    cc[m] = f2_fma(c2, c2, cc[m]);
+    cs[m] = f2_fma(c2, s2, cs[m]);
+    if (m + 1 < K) {
+      const f2_t tc = f2_mul(c2, cr2);
+      const f2_t tsr = f2_mul(s2, cr2);
+      const f2_t cn = f2_fma(s2, nsr2, tc);
+      s2 = f2_fma(c2, sr2, tsr);
+      c2 = cn;
+    }
+  }
+}
+
 template <int K>
 __global__ void __launch_bounds__(256) main_f32_packed(MainParams<RecF32, float> p) {
   constexpr int F = 2 * K;
-  __shared__ uint4 s_rec[2 * LSP_TILE_OBS];
-  __shared__ double red_p[32];
-  __shared__ int64_t red_k[32];
+  __shared__ uint4 s_obs[2 * LSP_TILE_OBS];
+  __shared__ unsigned long long red[32];
   __shared__ uint32_t s_item;
   extern __shared__ __align__(16) unsigned char dyn_smem[];
   float* s_pw = reinterpret_cast<float*>(dyn_smem);
   const int tid = threadIdx.x;
+  const uint32_t n_items = (uint32_t)p.n_items;
+  const uint32_t split = (uint32_t)p.split, n_chunks = (uint32_t)p.n_chunks;
 
   for (;;) {
     if (tid == 0) s_item = atomicAdd(p.queue, 1u);
     __syncthreads();
-    const int64_t item = s_item;
+    const uint32_t item = s_item;
     __syncthreads();
-    if (item >= p.n_items) break;
-    const Item it = decode_item(p, item);
-    const ObjInfo oi = p.obj[it.o];
-    const int64_t kc0 = (int64_t)it.chunk * blockDim.x * F;
+    if (item >= n_items) break;
+    const uint32_t is = item % split;
+    const uint32_t oc = item / split;
+    const uint32_t chunk = oc % n_chunks;
+    const uint32_t orank = oc / n_chunks;
+    const int64_t o = p.order ? (int64_t)p.order[orank] : (int64_t)orank;
+    const ObjInfo oi = p.obj[o];
+    const int64_t kc0 = (int64_t)chunk * blockDim.x * F;
     const uint32_t k0 = (uint32_t)(kc0 + (int64_t)tid * F);
     const uint32_t k1 = k0 + K;
-    int64_t ob = oi.begin + (int64_t)oi.n * it.s / p.split;
-    int64_t oe = oi.begin + (int64_t)oi.n * (it.s + 1) / p.split;
+    const int64_t ob = oi.begin + (int64_t)oi.n * is / split;
+    int64_t oe = oi.begin + (int64_t)oi.n * (is + 1) / split;
     if (oi.flags) oe = ob;  // flagged objects: zero power
 
     f2_t xc[K], xs[K], cc[K], cs[K];
@@ -123,41 +171,23 @@ __global__ void __launch_bounds__(256) main_f32_packed(MainParams<RecF32, float>
     for (int64_t ts = ob; ts < oe; ts += LSP_TILE_OBS) {
       const int nt = (int)((oe - ts) < LSP_TILE_OBS ? (oe - ts) : LSP_TILE_OBS);
       const uint4* src = reinterpret_cast<const uint4*>(p.rec + ts);
-      for (int i = tid; i < 2 * nt; i += blockDim.x) s_rec[i] = __ldg(src + i);
+      for (int i = tid; i < 2 * nt; i += blockDim.x) s_obs[i] = __ldg(src + i);
       __syncthreads();
       for (int j = 0; j < nt; ++j) {
-        const uint4 r0 = s_rec[2 * j];
-        const uint4 r1 = s_rec[2 * j + 1];
-        const float y = __uint_as_float(r0.x);
-        const float cr = __uint_as_float(r0.y);
-        const float sr = __uint_as_float(r0.z);
-        float c0, s0, c1, s1;
-        seed_sincos_f32(phase_hi32(r0.w, r1.x, r1.y, k0), c0, s0);
-        seed_sincos_f32(phase_hi32(r0.w, r1.x, r1.y, k1), c1, s1);
-        f2_t c2 = f2_pack(c0, c1), s2 = f2_pack(s0, s1);
-        const f2_t y2 = f2_pack(y, y), cr2 = f2_pack(cr, cr);
-        const f2_t sr2 = f2_pack(sr, sr), nsr2 = f2_pack(-sr, -sr);
-#pragma unroll
-        for (int m = 0; m < K; ++m) {
-          xc[m] = f2_fma(y2, c2, xc[m]);
-          xs[m] = f2_fma(y2, s2, xs[m]);
-          cc[m] = f2_fma(c2, c2, cc[m]);
-          cs[m] = f2_fma(c2, s2, cs[m]);
-          if (m + 1 < K) {
-            const f2_t tc = f2_mul(c2, cr2);
-            const f2_t tsr = f2_mul(s2, cr2);
-            const f2_t cn = f2_fma(s2, nsr2, tc);
-            s2 = f2_fma(c2, sr2, tsr);
-            c2 = cn;
-          }
-        }
+        const uint4 r0 = s_obs[2 * j];
+        const uint4 r1 = s_obs[2 * j + 1];
+        f2_t c2, s2;
+        seed_pair(make_uint4(r0.w, r1.x, r1.y, 0u), k0, k1, c2, s2);
+        const uint32_t nsr = r0.z ^ 0x80000000u;
+        recurrence_steps<K>(xc, xs, cc, cs, c2, s2, f2_of(r0.x, r0.x), f2_of(r0.y, r0.y),
+                            f2_of(r0.z, r0.z), f2_of(nsr, nsr));
       }
       __syncthreads();
     }
 
-    if (p.split == 1) {
+    if (split == 1) {
       float pv[F];
-      const float nf = (float)oi.n, scale = (float)oi.norm_scale;
+      const float nf = (float)oi.n, scale = oi.norm_scale_f;
       uint32_t bad = 0u;
 #pragma unroll
       for (int m = 0; m < K; ++m) {
@@ -166,19 +196,19 @@ __global__ void __launch_bounds__(256) main_f32_packed(MainParams<RecF32, float>
         f2_unpack(xs[m], b0, b1);
         f2_unpack(cc[m], c0, c1);
         f2_unpack(cs[m], d0, d1);
-        pv[m] = scale * lsp_power<float>(a0, b0, c0, d0, nf, EpsRel<float>::v);
-        pv[K + m] = scale * lsp_power<float>(a1, b1, c1, d1, nf, EpsRel<float>::v);
-        if (ill_conditioned_f32(c0, d0, nf) && (int64_t)k0 + m < p.n_f) bad |= 1u << m;
-        if (ill_conditioned_f32(c1, d1, nf) && (int64_t)k1 + m < p.n_f) bad |= 1u << (K + m);
+        bool ill0, ill1;
+        pv[m] = scale * lsp_power_f32(a0, b0, c0, d0, nf, ill0);
+        pv[K + m] = scale * lsp_power_f32(a1, b1, c1, d1, nf, ill1);
+        if (ill0 && (int64_t)k0 + m < p.n_f) bad |= 1u << m;
+        if (ill1 && (int64_t)k1 + m < p.n_f) bad |= 1u << (K + m);
       }
       if (oi.flags) bad = 0u;
       fix_ill_conditioned<F>(pv, bad, k0, p.rec, oi.begin, oi.n, oi.norm_scale);
-      if (p.power_out) store_row<F>(p.power_out + it.o * p.n_f, (int64_t)k0, pv, p.n_f);
-      const int64_t res = it.o * p.n_chunks + it.chunk;
-      chunk_results<float, F>(pv, (int64_t)k0, kc0, p.n_f, p.best + res,
-                              p.cand ? p.cand + res : nullptr, s_pw, red_p, red_k);
+      if (p.power_out) store_row<F>(p.power_out + o * p.n_f, (int64_t)k0, pv, p.n_f);
+      const int64_t res = o * (int64_t)n_chunks + chunk;
+      chunk_results_f32<F>(pv, k0, kc0, p.n_f, p.best + res, p.cand ? p.cand + res : nullptr, s_pw, red);
     } else {
-      float* part = p.part + (int64_t)it.s * p.n_f * 4;
+      float* part = p.part + (int64_t)is * p.n_f * 4;
 #pragma unroll
       for (int m = 0; m < K; ++m) {
         float a0, a1, b0, b1, c0, c1, d0, d1;
@@ -259,23 +289,30 @@ __global__ void __launch_bounds__(256) main_scalar(MainParams<Rec, Real> p) {
 
     if (p.split == 1) {
       Real pv[F];
-      const Real nf = (Real)oi.n, scale = (Real)oi.norm_scale;
-      uint32_t bad = 0u;
-#pragma unroll
-      for (int m = 0; m < K; ++m) {
-        pv[m] = scale * lsp_power<Real>(xc[m], xs[m], cc[m], cs[m], nf, EpsRel<Real>::v);
-        if constexpr (std::is_same<Real, float>::value) {
-          if (ill_conditioned_f32(cc[m], cs[m], nf) && (int64_t)k0 + m < p.n_f) bad |= 1u << m;
-        }
-      }
+      const int64_t res = it.o * p.n_chunks + it.chunk;
       if constexpr (std::is_same<Real, float>::value) {
+        const float nf = (float)oi.n, scale = oi.norm_scale_f;
+        uint32_t bad = 0u;
+#pragma unroll
+        for (int m = 0; m < K; ++m) {
+          bool ill;
+          pv[m] = scale * lsp_power_f32(xc[m], xs[m], cc[m], cs[m], nf, ill);
+          if (ill && (int64_t)k0 + m < p.n_f) bad |= 1u << m;
+        }
         if (oi.flags) bad = 0u;
         fix_ill_conditioned<F>(pv, bad, k0, p.rec, oi.begin, oi.n, oi.norm_scale);
+        if (p.power_out) store_row<F>(p.power_out + it.o * p.n_f, (int64_t)k0, pv, p.n_f);
+        chunk_results_f32<F>(pv, k0, kc0, p.n_f, p.best + res, p.cand ? p.cand + res : nullptr,
+                             reinterpret_cast<float*>(s_pw), reinterpret_cast<unsigned long long*>(red_p));
+      } else {
+        const Real nf = (Real)oi.n, scale = (Real)oi.norm_scale;
+#pragma unroll
+        for (int m = 0; m < K; ++m)
+          pv[m] = scale * lsp_power<Real>(xc[m], xs[m], cc[m], cs[m], nf, EpsRel<Real>::v);
+        if (p.power_out) store_row<F>(p.power_out + it.o * p.n_f, (int64_t)k0, pv, p.n_f);
+        chunk_results<Real, F>(pv, (int64_t)k0, kc0, p.n_f, p.best + res,
+                               p.cand ? p.cand + res : nullptr, s_pw, red_p, red_k);
       }
-      if (p.power_out) store_row<F>(p.power_out + it.o * p.n_f, (int64_t)k0, pv, p.n_f);
-      const int64_t res = it.o * p.n_chunks + it.chunk;
-      chunk_results<Real, F>(pv, (int64_t)k0, kc0, p.n_f, p.best + res,
-                             p.cand ? p.cand + res : nullptr, s_pw, red_p, red_k);
     } else {
       Real* part = p.part + (int64_t)it.s * p.n_f * 4;
 #pragma unroll

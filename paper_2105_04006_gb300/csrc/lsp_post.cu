@@ -66,9 +66,12 @@ __global__ void __launch_bounds__(kCombineThreads) combine_kernel(
         cs += q[3];
       }
     }
-    pv[m] = oi.flags ? Real(0) : scale * lsp_power<Real>(xc, xs, cc, cs, nf, EpsRel<Real>::v);
     if constexpr (std::is_same<Real, float>::value) {
-      if (k < n_f && !oi.flags && ill_conditioned_f32(cc, cs, nf)) bad |= 1u << m;
+      bool ill;
+      pv[m] = oi.flags ? 0.0f : oi.norm_scale_f * lsp_power_f32(xc, xs, cc, cs, nf, ill);
+      if (k < n_f && !oi.flags && ill) bad |= 1u << m;
+    } else {
+      pv[m] = oi.flags ? Real(0) : scale * lsp_power<Real>(xc, xs, cc, cs, nf, EpsRel<Real>::v);
     }
   }
   if constexpr (std::is_same<Real, float>::value)
@@ -78,8 +81,12 @@ __global__ void __launch_bounds__(kCombineThreads) combine_kernel(
     for (int m = 0; m < NP; ++m)
       if (k0 + m < n_f) power_out[k0 + m] = pv[m];
   }
-  chunk_results<Real, NP>(pv, k0, kc0, n_f, best + blockIdx.x, cand ? cand + blockIdx.x : nullptr,
-                          s_pw, red_p, red_k);
+  if constexpr (std::is_same<Real, float>::value)
+    chunk_results_f32<NP>(pv, (uint32_t)k0, kc0, n_f, best + blockIdx.x, cand ? cand + blockIdx.x : nullptr,
+                          reinterpret_cast<float*>(s_pw), reinterpret_cast<unsigned long long*>(red_p));
+  else
+    chunk_results<Real, NP>(pv, k0, kc0, n_f, best + blockIdx.x, cand ? cand + blockIdx.x : nullptr,
+                            s_pw, red_p, red_k);
 }
 
 __device__ __forceinline__ lsp_peak make_peak(int64_t k, double p, double f_min, double df,

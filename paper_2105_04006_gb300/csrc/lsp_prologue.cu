@@ -117,6 +117,8 @@ __global__ void stats_kernel(const double* __restrict__ t, const YT* __restrict_
     oi.n = (int32_t)n;
     oi.flags = flags;
     oi.norm_scale = (norm && s2 > 0.0) ? 2.0 / s2 : 1.0;
+    oi.norm_scale_f = (float)oi.norm_scale;
+    oi.pad[0] = oi.pad[1] = oi.pad[2] = 0;
     obj[o] = oi;
   }
 }

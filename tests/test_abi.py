@@ -124,3 +124,22 @@ def test_binding_fails_loudly_without_library(tmp_path, monkeypatch):
     monkeypatch.setattr(lsp, "_lib", None)
     with pytest.raises(lsp.LibraryNotBuilt):
         lsp.lib()
+
+
+def test_grid_rule_reproduces_table2(lsp_mod):
+    """Section 4.3 / Table 2: df = 0.2 pi / T_max (angular), N_f = (f_max - f_min) / df.
+
+    The table prints f in rad/day and df to four digits; T_max follows from
+    df, and the library (cycles/day) must return the printed N_f.
+    """
+    import math
+    path = os.path.join(ROOT, "tests", "golden", "table2_grid.txt")
+    rows = [l.split() for l in open(path) if l.strip() and not l.startswith("#")]
+    assert len(rows) == 2
+    for name, f_min, f_max, df, n_f in rows:
+        f_min, f_max, df, n_f = float(f_min), float(f_max), float(df), int(n_f)
+        t_max = 0.2 * math.pi / df
+        g = lsp_mod.grid_for_span(f_min / (2 * math.pi), f_max / (2 * math.pi), t_max)
+        assert g.n_f == n_f, (name, g.n_f, n_f)
+    with pytest.raises(lsp_mod.LSPError):
+        lsp_mod.grid_for_span(1.0, 2.0, 0.0)
