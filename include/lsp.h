@@ -256,6 +256,100 @@ lsp_status lsp_plan_get_config(const lsp_plan* plan, lsp_config* config);
 lsp_status lsp_plan_set_config(lsp_plan* plan, const lsp_config* config);
 void lsp_plan_destroy(lsp_plan* plan);
 
+/* ---- learned proposal stage ------------------------------------------------
+ * Not in the paper: a small MLP proposes, per light curve, the grid windows
+ * most likely to hold the periodogram's maximum; the direct method refines
+ * only those windows and falls back to the full grid when the refined peak
+ * is weak.  The network trains on light curves and periodograms that the
+ * direct method itself produces (lsp_batch labels).
+ *
+ * Parameters are one flat FP32 vector in the order W1, b1, W2, b2, ..., with
+ * W_l row-major of shape (fan_in, fan_out), plus its bfloat16 copy (same
+ * layout; the GEMMs read the weights from the copy and the biases from the
+ * FP32 vector).  bfloat16 arrays are passed as uint16_t.
+ */
+#define LSP_FEAT_DIM 512
+#define LSP_REFINE_FALLBACK 256 /* bit of lsp_refine_windows' info word */
+
+typedef struct lsp_mlp_dims {
+  int32_t in_dim;    /* LSP_FEAT_DIM for lsp_featurize inputs */
+  int32_t hidden;    /* width of each hidden layer */
+  int32_t n_hidden;  /* hidden layers, 1..6 (Linear + ReLU each) */
+  int32_t n_classes; /* output logits: one per refinement window */
+} lsp_mlp_dims;
+
+/* Length of the flat parameter vector. */
+lsp_status lsp_mlp_param_count(const lsp_mlp_dims* dims, int64_t* count);
+/* Scratch bytes of lsp_mlp_forward / lsp_mlp_loss_grad for a batch. */
+lsp_status lsp_mlp_workspace_size(const lsp_mlp_dims* dims, int64_t batch, size_t* bytes);
+
+/*
+ * 512 features per light curve (CSR batch as in lsp_batch; y float):
+ * with z the standardised magnitudes and all pairs i < j with
+ * |t_j - t_i| < lag_max, features 0..255 are the short-lag periodogram
+ * sum_pairs z_i z_j cos(2 pi f_c dt) / (pairs + 1) at the 256 coarse bin
+ * centres f_c of [f_min, f_max), and features 256..511 are log(1 + pairs)
+ * in 256 equal lag bins of [0, lag_max).  feat_bf16 (n_obj x 512) is
+ * required, feat_f32 optional.  Objects with fewer than two observations or
+ * zero variance get zeros.
+ */
+lsp_status lsp_featurize(const double* t, const float* y, const int64_t* offsets, int64_t n_obj,
+                         int64_t total_nt, const lsp_grid* grid, float lag_max, uint16_t* feat_bf16,
+                         float* feat_f32, lsp_stream_t stream);
+
+/* Logits (batch x n_classes, FP32) of the MLP on bfloat16 inputs x (batch x in_dim). */
+lsp_status lsp_mlp_forward(const lsp_mlp_dims* dims, const float* params, const uint16_t* params_bf16,
+                           const uint16_t* x_bf16, int64_t batch, float* logits, void* workspace,
+                           size_t ws_bytes, lsp_stream_t stream);
+
+/*
+ * Mean softmax cross-entropy of the batch against labels (class indices)
+ * into *loss (device float) and its gradient into grad (flat FP32, the
+ * parameters' layout).  Hidden activations and back-propagated
+ * pre-activation gradients are stored in bfloat16; products accumulate in
+ * FP32 on the tensor cores.
+ */
+lsp_status lsp_mlp_loss_grad(const lsp_mlp_dims* dims, const float* params, const uint16_t* params_bf16,
+                             const uint16_t* x_bf16, const int32_t* labels, int64_t batch, float* loss,
+                             float* grad, void* workspace, size_t ws_bytes, lsp_stream_t stream);
+
+/* One AdamW step (decoupled weight decay; step counts from 1) on the FP32
+ * parameters; refreshes the bfloat16 copy. */
+lsp_status lsp_mlp_adamw(int64_t n, float* params, uint16_t* params_bf16, const float* grad, float* m,
+                         float* v, int64_t step, float lr, float beta1, float beta2, float eps,
+                         float weight_decay, lsp_stream_t stream);
+
+/* FP32 -> bfloat16 (round to nearest even). */
+lsp_status lsp_to_bf16(const float* a, uint16_t* b, int64_t n, lsp_stream_t stream);
+
+/* The k (<= 16) largest logits' classes per row, largest first, ties to the lower class. */
+lsp_status lsp_top_classes(const float* logits, int64_t rows, int32_t n_classes, int32_t k,
+                           int32_t* classes, lsp_stream_t stream);
+
+lsp_status lsp_refine_workspace_size(int64_t n_obj, int64_t total_nt, const lsp_grid* grid,
+                                     size_t* bytes);
+
+/*
+ * Refine proposed windows, then fall back.  classes (n_obj x k_windows,
+ * best first) name windows: class c covers bins
+ * [c*stride + stride/2 - window/2, +window) moved inside the grid
+ * (window <= 2048).  Windows are evaluated in rank order with the FP32 direct
+ * method; an object stops once its best refined power reaches stop_power.
+ * Objects whose best refined power is below fallback_power get the full
+ * grid, and so do, when inconclusive_fallback is nonzero, objects that
+ * evaluated all k_windows windows without reaching stop_power (for short
+ * light curves a noise peak in a wrong window can exceed fallback_power).
+ * peaks[o] is the result (first maximum of what was evaluated);
+ * info[o] (nullable) = windows evaluated | LSP_REFINE_FALLBACK if the full
+ * grid was used.  norm is an lsp_norm; thresholds are in that normalisation.
+ */
+lsp_status lsp_refine_windows(const double* t, const float* y, const int64_t* offsets, int64_t n_obj,
+                              int64_t total_nt, const lsp_grid* grid, int32_t norm,
+                              const int32_t* classes, int32_t k_windows, int64_t window,
+                              int64_t stride, float stop_power, float fallback_power,
+                              int32_t inconclusive_fallback, lsp_peak* peaks, int32_t* info,
+                              void* workspace, size_t ws_bytes, lsp_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -78,7 +78,15 @@ EXPORTS = [
     "lsp_plan_execute_host", "lsp_plan_autotune", "lsp_plan_get_config", "lsp_plan_set_config",
     "lsp_plan_destroy", "lsp_plan_enable_timing", "lsp_plan_main_kernel_ms", "lsp_plan_kernel_count",
     "lsp_batch_noalloc", "lsp_grid_for_span",
+    "lsp_mlp_param_count", "lsp_mlp_workspace_size", "lsp_featurize", "lsp_mlp_forward",
+    "lsp_mlp_loss_grad", "lsp_mlp_adamw", "lsp_to_bf16", "lsp_top_classes", "lsp_refine_workspace_size",
+    "lsp_refine_windows",
 ]
+
+
+class MlpDims(ctypes.Structure):
+    _fields_ = [("in_dim", ctypes.c_int32), ("hidden", ctypes.c_int32), ("n_hidden", ctypes.c_int32),
+                ("n_classes", ctypes.c_int32)]
 
 
 def lib():
@@ -113,6 +121,19 @@ def lib():
             L.lsp_plan_enable_timing.argtypes = [P, i32]
             L.lsp_plan_main_kernel_ms.argtypes = [P, ctypes.POINTER(ctypes.c_float)]
             L.lsp_plan_kernel_count.argtypes = [P, ctypes.POINTER(i32)]
+            DP = ctypes.POINTER(MlpDims)
+            f32 = ctypes.c_float
+            L.lsp_mlp_param_count.argtypes = [DP, ctypes.POINTER(i64)]
+            L.lsp_mlp_workspace_size.argtypes = [DP, i64, ctypes.POINTER(sz)]
+            L.lsp_featurize.argtypes = [P, P, P, i64, i64, GP, f32, P, P, P]
+            L.lsp_mlp_forward.argtypes = [DP, P, P, P, i64, P, P, sz, P]
+            L.lsp_mlp_loss_grad.argtypes = [DP, P, P, P, P, i64, P, P, P, sz, P]
+            L.lsp_mlp_adamw.argtypes = [i64, P, P, P, P, P, i64, f32, f32, f32, f32, f32, P]
+            L.lsp_to_bf16.argtypes = [P, P, i64, P]
+            L.lsp_top_classes.argtypes = [P, i64, i32, i32, P, P]
+            L.lsp_refine_workspace_size.argtypes = [i64, i64, GP, ctypes.POINTER(sz)]
+            L.lsp_refine_windows.argtypes = [P, P, P, i64, i64, GP, i32, P, i32, i64, i64, f32, f32, i32, P,
+                                             P, P, sz, P]
             L.lsp_plan_destroy.argtypes = [P]
             L.lsp_plan_destroy.restype = None
             for name in EXPORTS:

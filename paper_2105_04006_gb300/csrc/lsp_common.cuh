@@ -91,6 +91,13 @@ struct MainParams {
   int32_t n_chunks;      // frequency chunks per object
   int32_t split;         // observation splits per chunk (1 = fused epilogue)
   int64_t n_items;       // n_obj * n_chunks * split
+  // Optional: the number of items read from device memory at kernel start
+  // (work lists built on the device), and per-object window origins (the
+  // learned stage's refinement windows: one chunk per listed object, bins
+  // [win_start[o], win_start[o] + win_len) of the grid).
+  const uint32_t* n_items_dev;
+  const int32_t* win_start;
+  int32_t win_len;
 };
 
 // ---------------------------------------------------------------- f32x2 ops

@@ -44,6 +44,9 @@ struct MainLaunch {
   int32_t n_chunks;
   int32_t split;
   int64_t n_items;
+  const uint32_t* n_items_dev = nullptr;  // device item count (overrides n_items)
+  const int32_t* win_start = nullptr;     // per-object window origins (packed FP32 kernels)
+  int32_t win_len = 0;
 };
 bool main_variant_exists(int prec, int packed, int k_reseed, int fpt);
 cudaError_t launch_main(const MainLaunch& ml, cudaStream_t stream);

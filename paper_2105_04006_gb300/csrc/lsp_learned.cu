@@ -1,0 +1,893 @@
+// lsp_learned.cu -- the learned-proposal stage: featurizer, MLP forward /
+// backward / AdamW on the tensor cores, proposal of refinement windows, and
+// the windowed refine + full-grid fallback built on the main kernel.
+//
+// The paper has no learned component.  The stage proposes, for each light
+// curve, the grid windows most likely to hold the periodogram's maximum; the
+// direct method then refines only those windows and falls back to the full
+// grid when the refined peak is weak.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <cuda_bf16.h>
+
+#include "../../include/lsp.h"
+#include "lsp_launch.h"
+
+namespace lsp {
+void set_last_error(const char* msg);
+}
+
+using namespace lsp;
+
+namespace {
+
+typedef __nv_bfloat16 bf16;
+
+lsp_status err_arg(const char* msg) {
+  set_last_error(msg);
+  return LSP_E_ARG;
+}
+lsp_status err_cuda(cudaError_t e, const char* what) {
+  char buf[256];
+  snprintf(buf, sizeof buf, "%s: %s", what, cudaGetErrorString(e));
+  set_last_error(buf);
+  return LSP_E_CUDA;
+}
+#define LEARN_CUDA(call, what)                        \
+  do {                                                \
+    cudaError_t e__ = (call);                         \
+    if (e__ != cudaSuccess) return err_cuda(e__, what); \
+  } while (0)
+
+size_t align256(size_t x) { return (x + 255) / 256 * 256; }
+
+// =============================================================== featurizer
+// One CTA of 256 threads per light curve.  For a time-sorted light curve each
+// thread walks the band of observations after its own until the lag reaches
+// lag_max, four candidates per step; otherwise all n^2 candidate pairs are
+// scanned in flat blocks of 1024.  Pairs with |t_j - t_i| < lag_max go to a
+// shared buffer in scan order (a block-wide prefix sum keeps the order, and so
+// the float sums, deterministic).  Thread c then adds w cos(2 pi f_c dt) for
+// every buffered pair to coarse bin c; the lag histogram counts pairs per lag
+// bin.
+constexpr int kFeatThreads = 256;
+constexpr int kCoarse = 256;
+constexpr int kLagBins = 256;
+constexpr int kPairBlock = 4 * kFeatThreads;
+
+__global__ void __launch_bounds__(kFeatThreads) featurize_kernel(
+    const double* __restrict__ t, const float* __restrict__ y, const int64_t* __restrict__ offsets,
+    int64_t total_nt, double f_min, double f_max, float lag_max, bf16* __restrict__ feat16,
+    float* __restrict__ feat32) {
+  __shared__ float s_dt[kPairBlock];
+  __shared__ float s_w[kPairBlock];
+  __shared__ uint32_t s_hist[kLagBins];
+  __shared__ int s_scan[kFeatThreads / 32];
+  __shared__ double s_red[32];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int64_t o = blockIdx.x;
+  int64_t b = offsets[o], e = offsets[o + 1];
+  if (b < 0 || e < b || e > total_nt) b = e = 0;
+  const int n = (int)(e - b);
+  s_hist[tid] = 0u;
+  // mean and rms of y (FP64)
+  double sy = 0.0;
+  for (int j = tid; j < n; j += kFeatThreads) sy += (double)y[b + j];
+  for (int off = 16; off > 0; off >>= 1) sy += __shfl_xor_sync(0xffffffffu, sy, off);
+  if (lane == 0) s_red[warp] = sy;
+  __syncthreads();
+  double tot = 0.0;
+  for (int w = 0; w < kFeatThreads / 32; ++w) tot += s_red[w];
+  const double mean = n > 0 ? tot / n : 0.0;
+  __syncthreads();
+  double s2 = 0.0;
+  for (int j = tid; j < n; j += kFeatThreads) {
+    const double d = (double)y[b + j] - mean;
+    s2 += d * d;
+  }
+  for (int off = 16; off > 0; off >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, off);
+  if (lane == 0) s_red[warp] = s2;
+  __syncthreads();
+  double var = 0.0;
+  for (int w = 0; w < kFeatThreads / 32; ++w) var += s_red[w];
+  var = n > 0 ? var / n : 0.0;
+  const bool ok = n >= 2 && var > 0.0;
+  const float rstd = ok ? (float)(1.0 / sqrt(var)) : 0.0f;
+  const float fc = (float)(f_min + (tid + 0.5) * (f_max - f_min) / kCoarse);
+  const float lag_scale = kLagBins / lag_max;
+  float acc = 0.0f;
+  uint32_t n_pairs = 0u;
+  // time-sorted light curves (the usual case) only need the short-lag band
+  // after each observation; others are scanned over all n^2 candidates
+  int unsorted = 0;
+  for (int j = tid + 1; j < n; j += kFeatThreads) unsorted |= t[b + j] < t[b + j - 1];
+  const bool sorted = !__syncthreads_or(unsorted);
+
+  // Buffers the (up to four) pairs each thread found, in flat order, then
+  // adds every buffered pair to this thread's coarse bin.
+  auto flush = [&](int cnt, const float (&dt)[4], const float (&w)[4]) {
+    int incl = cnt;
+    for (int off = 1; off < 32; off <<= 1) {
+      const int v = __shfl_up_sync(0xffffffffu, incl, off);
+      if (lane >= off) incl += v;
+    }
+    if (lane == 31) s_scan[warp] = incl;
+    __syncthreads();
+    int wbase = 0, total = 0;
+    for (int ww = 0; ww < kFeatThreads / 32; ++ww) {
+      if (ww < warp) wbase += s_scan[ww];
+      total += s_scan[ww];
+    }
+    const int at = wbase + incl - cnt;
+    for (int q = 0; q < cnt; ++q) {
+      s_dt[at + q] = dt[q];
+      s_w[at + q] = w[q];
+      int lb = (int)(dt[q] * lag_scale);
+      lb = lb < kLagBins - 1 ? lb : kLagBins - 1;
+      atomicAdd(&s_hist[lb], 1u);
+    }
+    __syncthreads();
+    for (int q = 0; q < total; ++q) {
+      const float ph = fc * s_dt[q];  // cycles; |ph| < 12 * 16
+      const float x = ph - rintf(ph);
+      acc = fmaf(s_w[q], __cosf(6.28318530717958647692f * x), acc);
+    }
+    n_pairs += (uint32_t)total;
+    __syncthreads();
+  };
+  auto pair_of = [&](int i, int j, float (&dt)[4], float (&w)[4], int& cnt) {
+    const double d = fabs(t[b + j] - t[b + i]);
+    if (d < (double)lag_max) {
+      dt[cnt] = (float)d;
+      w[cnt] = (float)(((double)y[b + i] - mean) * ((double)y[b + j] - mean)) * rstd * rstd;
+      ++cnt;
+    }
+    return d;
+  };
+
+  if (ok && sorted) {
+    for (int ib = 0; ib < n; ib += kFeatThreads) {
+      const int i = ib + tid;
+      bool more = true;
+      for (int q = 0;; ++q) {
+        float dt[4] = {0.f, 0.f, 0.f, 0.f}, w[4] = {0.f, 0.f, 0.f, 0.f};
+        int cnt = 0;
+        if (i < n && more) {
+          for (int r = 0; r < 4; ++r) {
+            const int j = i + 1 + 4 * q + r;
+            if (j >= n || pair_of(i, j, dt, w, cnt) >= (double)lag_max) {
+              more = false;
+              break;
+            }
+          }
+        } else {
+          more = false;
+        }
+        flush(cnt, dt, w);
+        if (!__syncthreads_or(more)) break;
+      }
+    }
+  } else if (ok) {
+    const int64_t n_cand = (int64_t)n * n;
+    for (int64_t base = 0; base < n_cand; base += kPairBlock) {
+      float dt[4] = {0.f, 0.f, 0.f, 0.f}, w[4] = {0.f, 0.f, 0.f, 0.f};
+      int cnt = 0;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int64_t flat = base + (int64_t)tid * 4 + q;
+        if (flat < n_cand) {
+          const int i = (int)(flat / n), j = (int)(flat % n);
+          if (j > i) pair_of(i, j, dt, w, cnt);
+        }
+      }
+      flush(cnt, dt, w);
+    }
+  }
+  const float f_c = ok ? acc / (float)(n_pairs + 1u) : 0.0f;
+  const float f_l = ok ? log1pf((float)s_hist[tid]) : 0.0f;
+  feat16[o * LSP_FEAT_DIM + tid] = __float2bfloat16_rn(f_c);
+  feat16[o * LSP_FEAT_DIM + kCoarse + tid] = __float2bfloat16_rn(f_l);
+  if (feat32) {
+    feat32[o * LSP_FEAT_DIM + tid] = f_c;
+    feat32[o * LSP_FEAT_DIM + kCoarse + tid] = f_l;
+  }
+}
+
+// ===================================================================== GEMM
+// C[M, N] = A[M, K] B[K, N] on the tensor cores (mma.sync m16n8k16, bf16 in,
+// fp32 accumulate).  A and B are read through element strides, so the same
+// kernel serves X W, dZ W^T and A^T dZ.  Epilogue: optional bias (fp32),
+// ReLU, multiplication by the ReLU mask (mask > 0) of a bf16 matrix, and
+// fp32 and/or bf16 outputs (row-major, leading dimension N).
+struct GemmArgs {
+  int M, N, K;
+  const bf16* A;
+  int64_t a_m, a_k;
+  const bf16* B;
+  int64_t b_k, b_n;
+  const float* bias;
+  int relu;
+  const bf16* mask;
+  float* C32;
+  bf16* C16;
+};
+
+constexpr int BM = 64, BN = 64, BK = 32, GEMM_THREADS = 128;
+
+__device__ __forceinline__ uint32_t pack_bf16(bf16 lo, bf16 hi) {
+  return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
+}
+
+__global__ void __launch_bounds__(GEMM_THREADS) gemm_bf16_kernel(GemmArgs g) {
+  __shared__ bf16 As[BM][BK + 8];
+  __shared__ bf16 Bs[BK][BN + 8];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int gid = lane >> 2, tig = lane & 3;
+  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+  const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
+  float acc[2][4][4];
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) acc[a][b][c] = 0.0f;
+  const bf16 zero = __float2bfloat16_rn(0.0f);
+  for (int k0 = 0; k0 < g.K; k0 += BK) {
+    for (int idx = tid; idx < BM * BK; idx += GEMM_THREADS) {
+      const int r = idx / BK, c = idx % BK;
+      const int m = m0 + r, k = k0 + c;
+      As[r][c] = (m < g.M && k < g.K) ? g.A[(int64_t)m * g.a_m + (int64_t)k * g.a_k] : zero;
+    }
+    for (int idx = tid; idx < BK * BN; idx += GEMM_THREADS) {
+      const int r = idx / BN, c = idx % BN;
+      const int k = k0 + r, n = n0 + c;
+      Bs[r][c] = (k < g.K && n < g.N) ? g.B[(int64_t)k * g.b_k + (int64_t)n * g.b_n] : zero;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < BK; kk += 16) {
+      uint32_t af[2][4], bfr[4][2];
+#pragma unroll
+      for (int mt = 0; mt < 2; ++mt) {
+        const int r = wm + mt * 16 + gid, c = kk + 2 * tig;
+        af[mt][0] = pack_bf16(As[r][c], As[r][c + 1]);
+        af[mt][1] = pack_bf16(As[r + 8][c], As[r + 8][c + 1]);
+        af[mt][2] = pack_bf16(As[r][c + 8], As[r][c + 9]);
+        af[mt][3] = pack_bf16(As[r + 8][c + 8], As[r + 8][c + 9]);
+      }
+#pragma unroll
+      for (int nt = 0; nt < 4; ++nt) {
+        const int c = wn + nt * 8 + gid, r = kk + 2 * tig;
+        bfr[nt][0] = pack_bf16(Bs[r][c], Bs[r + 1][c]);
+        bfr[nt][1] = pack_bf16(Bs[r + 8][c], Bs[r + 9][c]);
+      }
+#pragma unroll
+      for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+        for (int nt = 0; nt < 4; ++nt) {
+          float* d = acc[mt][nt];
+          asm volatile(
+              "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+              "{%8,%9}, {%0,%1,%2,%3};"
+              : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+              : "r"(af[mt][0]), "r"(af[mt][1]), "r"(af[mt][2]), "r"(af[mt][3]), "r"(bfr[nt][0]),
+                "r"(bfr[nt][1]));
+        }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+    for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+      for (int h = 0; h < 2; ++h)
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+          const int m = m0 + wm + mt * 16 + gid + 8 * h;
+          const int n = n0 + wn + nt * 8 + 2 * tig + q;
+          if (m >= g.M || n >= g.N) continue;
+          float v = acc[mt][nt][2 * h + q];
+          if (g.bias) v += g.bias[n];
+          if (g.relu) v = fmaxf(v, 0.0f);
+          const int64_t at = (int64_t)m * g.N + n;
+          if (g.mask && !(__bfloat162float(g.mask[at]) > 0.0f)) v = 0.0f;
+          if (g.C32) g.C32[at] = v;
+          if (g.C16) g.C16[at] = __float2bfloat16_rn(v);
+        }
+}
+
+cudaError_t gemm(const GemmArgs& g, cudaStream_t s) {
+  if (g.M <= 0 || g.N <= 0) return cudaSuccess;
+  dim3 grid((g.N + BN - 1) / BN, (g.M + BM - 1) / BM);
+  gemm_bf16_kernel<<<grid, GEMM_THREADS, 0, s>>>(g);
+  return cudaGetLastError();
+}
+
+// ============================================ loss, reductions, optimizer
+// One warp per row: mean softmax cross-entropy terms and dZ = (softmax -
+// onehot) / batch in bf16.
+__global__ void xent_kernel(const float* __restrict__ logits, const int32_t* __restrict__ labels,
+                            int64_t batch, int n_cls, float* __restrict__ row_loss,
+                            bf16* __restrict__ dz) {
+  const int64_t r = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (r >= batch) return;
+  const float* z = logits + r * n_cls;
+  float m = -INFINITY;
+  for (int c = lane; c < n_cls; c += 32) m = fmaxf(m, z[c]);
+  for (int off = 16; off > 0; off >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, off));
+  float s = 0.0f;
+  for (int c = lane; c < n_cls; c += 32) s += expf(z[c] - m);
+  for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+  int lab = labels[r];
+  lab = lab < 0 ? 0 : (lab >= n_cls ? n_cls - 1 : lab);
+  const float inv_b = 1.0f / (float)batch;
+  for (int c = lane; c < n_cls; c += 32) {
+    const float p = expf(z[c] - m) / s;
+    dz[r * n_cls + c] = __float2bfloat16_rn((p - (c == lab ? 1.0f : 0.0f)) * inv_b);
+  }
+  if (lane == 0) row_loss[r] = logf(s) + m - z[lab];
+}
+
+// Deterministic mean of n values (one CTA).
+__global__ void mean_kernel(const float* __restrict__ v, int64_t n, float* out) {
+  __shared__ double sh[32];
+  double s = 0.0;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) s += (double)v[i];
+  for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
+    *out = (float)(t / (double)(n > 0 ? n : 1));
+  }
+}
+
+// Column sums of a bf16 [rows x cols] matrix (bias gradients), fixed order.
+__global__ void colsum_kernel(const bf16* __restrict__ m, int64_t rows, int cols, float* __restrict__ out) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= cols) return;
+  float s = 0.0f;
+  for (int64_t r = 0; r < rows; ++r) s += __bfloat162float(m[r * cols + c]);
+  out[c] = s;
+}
+
+__global__ void adamw_kernel(int64_t n, float* __restrict__ p, bf16* __restrict__ p16,
+                             const float* __restrict__ g, float* __restrict__ m, float* __restrict__ v,
+                             float lr, float b1, float b2, float eps, float wd, float bc1, float bc2) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.0f - b1) * gi;
+    const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    const float upd = (mi / bc1) / (sqrtf(vi / bc2) + eps) + wd * p[i];
+    const float pi = p[i] - lr * upd;
+    p[i] = pi;
+    p16[i] = __float2bfloat16_rn(pi);
+  }
+}
+
+__global__ void to_bf16_kernel(int64_t n, const float* __restrict__ a, bf16* __restrict__ b) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    b[i] = __float2bfloat16_rn(a[i]);
+}
+
+// Top-k classes per row of logits (k <= 16), ties to the lower class.
+__global__ void topk_kernel(const float* __restrict__ logits, int64_t rows, int n_cls, int k,
+                            int32_t* __restrict__ out) {
+  const int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (r >= rows) return;
+  float tv[16];
+  int tc[16];
+  for (int i = 0; i < k; ++i) {
+    tv[i] = -INFINITY;
+    tc[i] = -1;
+  }
+  const float* z = logits + r * n_cls;
+  for (int c = 0; c < n_cls; ++c) {
+    const float v = z[c];
+    if (tc[k - 1] >= 0 && !(v > tv[k - 1])) continue;
+    int at = k - 1;
+    while (at > 0 && (tc[at - 1] < 0 || v > tv[at - 1])) {
+      tv[at] = tv[at - 1];
+      tc[at] = tc[at - 1];
+      --at;
+    }
+    tv[at] = v;
+    tc[at] = c;
+  }
+  for (int i = 0; i < k; ++i) out[r * k + i] = tc[i];
+}
+
+// ===================================================== refine + fallback
+// Per-object refinement state (in the workspace).
+struct RefineState {
+  double best_p;    // best refined power so far
+  int64_t best_k;   // its bin (-1: none)
+  int32_t rounds;   // windows evaluated
+  int16_t active;   // still refining
+  int16_t stopped;  // a window reached stop_power
+};
+
+// Full grid for objects whose refined peak is weak or, optionally, that
+// evaluated every proposed window without reaching stop_power.
+__device__ __forceinline__ bool needs_fallback(const RefineState& s, int flags, float fallback_power,
+                                               int inconclusive) {
+  return !flags && (s.best_p < (double)fallback_power || (inconclusive && !s.stopped));
+}
+
+// Window of class c: bins [c * stride + stride/2 - win/2, ... + win), moved
+// inside the grid.
+__device__ __forceinline__ int32_t window_start(int32_t c, int64_t stride, int64_t win, int64_t n_f) {
+  int64_t s = (int64_t)c * stride + stride / 2 - win / 2;
+  if (s + win > n_f) s = n_f - win;
+  if (s < 0) s = 0;
+  return (int32_t)s;
+}
+
+__global__ void refine_init(int64_t n_obj, const ObjInfo* __restrict__ obj, RefineState* st) {
+  const int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (o >= n_obj) return;
+  RefineState s;
+  s.best_p = 0.0;
+  s.best_k = -1;
+  s.rounds = 0;
+  s.active = obj[o].flags ? 0 : 1;
+  s.stopped = 0;
+  st[o] = s;
+}
+
+// List the active objects of round r and place their windows.
+__global__ void refine_list(int64_t n_obj, int r, int k_win, const int32_t* __restrict__ classes,
+                            int64_t stride, int64_t win, int64_t n_f, const RefineState* __restrict__ st,
+                            int32_t* __restrict__ win_start, int32_t* __restrict__ list,
+                            uint32_t* __restrict__ count) {
+  const int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (o >= n_obj) return;
+  if (!st[o].active) return;
+  int32_t c = classes[o * k_win + r];
+  if (c < 0) c = 0;
+  win_start[o] = window_start(c, stride, win, n_f);
+  const uint32_t at = atomicAdd(count, 1u);
+  list[at] = (int32_t)o;
+}
+
+__global__ void refine_merge(int64_t n_obj, int r, int k_win, float stop_power,
+                             const ChunkBest* __restrict__ round_best, RefineState* st) {
+  const int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (o >= n_obj) return;
+  RefineState s = st[o];
+  if (!s.active) return;
+  const ChunkBest b = round_best[o];
+  if (b.k >= 0 && (b.p > s.best_p || (b.p == s.best_p && (s.best_k < 0 || b.k < s.best_k)))) {
+    s.best_p = b.p;
+    s.best_k = b.k;
+  }
+  s.rounds = r + 1;
+  s.stopped = s.best_p >= (double)stop_power ? 1 : 0;
+  s.active = (!s.stopped && r + 1 < k_win) ? 1 : 0;
+  st[o] = s;
+}
+
+// Objects whose refined peak stays below fallback_power, and their item count.
+__global__ void fallback_list(int64_t n_obj, float fallback_power, int inconclusive,
+                              const ObjInfo* __restrict__ obj, const RefineState* __restrict__ st,
+                              int32_t* __restrict__ list, uint32_t* __restrict__ count) {
+  const int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (o >= n_obj) return;
+  if (!needs_fallback(st[o], obj[o].flags, fallback_power, inconclusive)) return;
+  const uint32_t at = atomicAdd(count, 1u);
+  list[at] = (int32_t)o;
+}
+
+__global__ void items_from_count(const uint32_t* count, uint32_t per, uint32_t* items) {
+  *items = *count * per;
+}
+
+__global__ void refine_finalize(int64_t n_obj, const ObjInfo* __restrict__ obj,
+                                const RefineState* __restrict__ st, float fallback_power, int inconclusive,
+                                const ChunkBest* __restrict__ full_best, int n_chunks, double f_min,
+                                double df, lsp_peak* __restrict__ peaks, int32_t* __restrict__ info) {
+  const int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (o >= n_obj) return;
+  const RefineState s = st[o];
+  const int flags = obj[o].flags;
+  double p = s.best_p;
+  int64_t k = s.best_k;
+  const bool fb = needs_fallback(s, flags, fallback_power, inconclusive);
+  if (fb) {  // full grid: first maximum over the chunks
+    p = 0.0;
+    k = -1;
+    for (int c = 0; c < n_chunks; ++c) {
+      const ChunkBest b = full_best[o * n_chunks + c];
+      if (b.k >= 0 && (k < 0 || b.p > p || (b.p == p && b.k < k))) {
+        p = b.p;
+        k = b.k;
+      }
+    }
+  }
+  lsp_peak pk;
+  pk.flags = flags;
+  pk.reserved = 0;
+  if (flags || k < 0) {
+    pk.idx = -1;
+    pk.power = 0.0;
+    pk.freq = 0.0;
+    pk.period = 0.0;
+  } else {
+    pk.idx = k;
+    pk.power = p;
+    pk.freq = __dadd_rn(f_min, __dmul_rn((double)k, df));
+    pk.period = 1.0 / pk.freq;
+  }
+  peaks[o] = pk;
+  if (info) info[o] = s.rounds | (fb ? LSP_REFINE_FALLBACK : 0);
+}
+
+// Flat parameter layout (see lsp.h): W1, b1, W2, b2, ..., W_L, b_L.
+struct Layers {
+  int n;
+  int in[8], out[8];
+  int64_t w_off[8], b_off[8];
+  int64_t total;
+};
+
+lsp_status make_layers(const lsp_mlp_dims* d, Layers* L) {
+  if (!d || d->in_dim < 1 || d->hidden < 1 || d->n_hidden < 1 || d->n_hidden > 6 || d->n_classes < 1)
+    return err_arg("bad MLP dimensions");
+  L->n = d->n_hidden + 1;
+  int64_t at = 0;
+  for (int l = 0; l < L->n; ++l) {
+    L->in[l] = l == 0 ? d->in_dim : d->hidden;
+    L->out[l] = l + 1 == L->n ? d->n_classes : d->hidden;
+    L->w_off[l] = at;
+    at += (int64_t)L->in[l] * L->out[l];
+    L->b_off[l] = at;
+    at += L->out[l];
+  }
+  L->total = at;
+  return LSP_OK;
+}
+
+// MLP scratch: hidden activations (bf16), logits (fp32), two dZ buffers
+// (bf16), per-row losses.
+struct MlpWs {
+  bf16* act[8];
+  float* logits;
+  bf16* dz[2];
+  float* row_loss;
+  size_t total;
+};
+
+void mlp_ws_layout(const Layers& L, int64_t batch, char* base, MlpWs* w) {
+  size_t off = 0;
+  int maxw = 0;
+  for (int l = 0; l < L.n; ++l) maxw = L.out[l] > maxw ? L.out[l] : maxw;
+  for (int l = 0; l + 1 < L.n; ++l) {
+    w->act[l] = (bf16*)(base + off);
+    off = align256(off + (size_t)batch * L.out[l] * sizeof(bf16));
+  }
+  w->logits = (float*)(base + off);
+  off = align256(off + (size_t)batch * L.out[L.n - 1] * sizeof(float));
+  for (int i = 0; i < 2; ++i) {
+    w->dz[i] = (bf16*)(base + off);
+    off = align256(off + (size_t)batch * maxw * sizeof(bf16));
+  }
+  w->row_loss = (float*)(base + off);
+  off = align256(off + (size_t)batch * sizeof(float));
+  w->total = off;
+}
+
+lsp_status mlp_forward_impl(const Layers& L, const float* p32, const bf16* p16, const bf16* x,
+                            int64_t batch, const MlpWs& w, cudaStream_t s) {
+  const bf16* a = x;
+  for (int l = 0; l < L.n; ++l) {
+    GemmArgs g;
+    memset(&g, 0, sizeof g);
+    g.M = (int)batch;
+    g.N = L.out[l];
+    g.K = L.in[l];
+    g.A = a;
+    g.a_m = L.in[l];
+    g.a_k = 1;
+    g.B = p16 + L.w_off[l];
+    g.b_k = L.out[l];
+    g.b_n = 1;
+    g.bias = p32 + L.b_off[l];
+    if (l + 1 < L.n) {
+      g.relu = 1;
+      g.C16 = w.act[l];
+      a = w.act[l];
+    } else {
+      g.C32 = w.logits;
+    }
+    LEARN_CUDA(gemm(g, s), "MLP forward GEMM");
+  }
+  return LSP_OK;
+}
+
+}  // namespace
+
+// ======================================================================= C ABI
+extern "C" {
+
+lsp_status lsp_mlp_param_count(const lsp_mlp_dims* dims, int64_t* count) {
+  if (!count) return err_arg("count is NULL");
+  Layers L;
+  lsp_status st = make_layers(dims, &L);
+  if (st) return st;
+  *count = L.total;
+  return LSP_OK;
+}
+
+lsp_status lsp_mlp_workspace_size(const lsp_mlp_dims* dims, int64_t batch, size_t* bytes) {
+  if (!bytes || batch < 1) return err_arg("bad batch or NULL bytes");
+  Layers L;
+  lsp_status st = make_layers(dims, &L);
+  if (st) return st;
+  MlpWs w;
+  mlp_ws_layout(L, batch, nullptr, &w);
+  *bytes = w.total;
+  return LSP_OK;
+}
+
+lsp_status lsp_featurize(const double* t, const float* y, const int64_t* offsets, int64_t n_obj,
+                         int64_t total_nt, const lsp_grid* grid, float lag_max, uint16_t* feat_bf16,
+                         float* feat_f32, lsp_stream_t stream) {
+  if (n_obj < 0 || n_obj > INT32_MAX || total_nt < 0) return err_arg("bad n_obj or total_nt");
+  if (n_obj == 0) return LSP_OK;
+  if (!grid || !(grid->f_max > grid->f_min)) return err_arg("bad grid");
+  if (!(lag_max > 0.0f)) return err_arg("lag_max must be > 0");
+  if (!offsets || !feat_bf16 || (total_nt > 0 && (!t || !y))) return err_arg("NULL array");
+  featurize_kernel<<<(unsigned)n_obj, kFeatThreads, 0, (cudaStream_t)stream>>>(
+      t, y, offsets, total_nt, grid->f_min, grid->f_max, lag_max, (bf16*)feat_bf16, feat_f32);
+  LEARN_CUDA(cudaGetLastError(), "featurize");
+  return LSP_OK;
+}
+
+lsp_status lsp_mlp_forward(const lsp_mlp_dims* dims, const float* params, const uint16_t* params_bf16,
+                           const uint16_t* x_bf16, int64_t batch, float* logits, void* workspace,
+                           size_t ws_bytes, lsp_stream_t stream) {
+  Layers L;
+  lsp_status st = make_layers(dims, &L);
+  if (st) return st;
+  if (batch < 1 || !params || !params_bf16 || !x_bf16 || !logits) return err_arg("NULL argument");
+  MlpWs w;
+  mlp_ws_layout(L, batch, (char*)workspace, &w);
+  if (!workspace || ws_bytes < w.total) return err_arg("MLP workspace too small");
+  w.logits = logits;
+  return mlp_forward_impl(L, params, (const bf16*)params_bf16, (const bf16*)x_bf16, batch, w,
+                          (cudaStream_t)stream);
+}
+
+lsp_status lsp_mlp_loss_grad(const lsp_mlp_dims* dims, const float* params, const uint16_t* params_bf16,
+                             const uint16_t* x_bf16, const int32_t* labels, int64_t batch, float* loss,
+                             float* grad, void* workspace, size_t ws_bytes, lsp_stream_t stream) {
+  Layers L;
+  lsp_status st = make_layers(dims, &L);
+  if (st) return st;
+  if (batch < 1 || !params || !params_bf16 || !x_bf16 || !labels || !loss || !grad)
+    return err_arg("NULL argument");
+  MlpWs w;
+  mlp_ws_layout(L, batch, (char*)workspace, &w);
+  if (!workspace || ws_bytes < w.total) return err_arg("MLP workspace too small");
+  cudaStream_t s = (cudaStream_t)stream;
+  const bf16* p16 = (const bf16*)params_bf16;
+  const bf16* x = (const bf16*)x_bf16;
+  if ((st = mlp_forward_impl(L, params, p16, x, batch, w, s))) return st;
+  const int n_cls = L.out[L.n - 1];
+  const int64_t warps_per_cta = 8;
+  xent_kernel<<<(unsigned)((batch + warps_per_cta - 1) / warps_per_cta), 256, 0, s>>>(
+      w.logits, labels, batch, n_cls, w.row_loss, w.dz[0]);
+  mean_kernel<<<1, 1024, 0, s>>>(w.row_loss, batch, loss);
+  LEARN_CUDA(cudaGetLastError(), "loss");
+  int cur = 0;
+  for (int l = L.n - 1; l >= 0; --l) {
+    const bf16* a_in = l == 0 ? x : w.act[l - 1];
+    // dW_l = A_in^T dZ_l  (in x out)
+    GemmArgs g;
+    memset(&g, 0, sizeof g);
+    g.M = L.in[l];
+    g.N = L.out[l];
+    g.K = (int)batch;
+    g.A = a_in;
+    g.a_m = 1;
+    g.a_k = L.in[l];
+    g.B = w.dz[cur];
+    g.b_k = L.out[l];
+    g.b_n = 1;
+    g.C32 = grad + L.w_off[l];
+    LEARN_CUDA(gemm(g, s), "MLP weight gradient");
+    colsum_kernel<<<(L.out[l] + 255) / 256, 256, 0, s>>>(w.dz[cur], batch, L.out[l], grad + L.b_off[l]);
+    if (l > 0) {
+      // dZ_{l-1} = (dZ_l W_l^T) * (A_{l-1} > 0)
+      GemmArgs h;
+      memset(&h, 0, sizeof h);
+      h.M = (int)batch;
+      h.N = L.in[l];
+      h.K = L.out[l];
+      h.A = w.dz[cur];
+      h.a_m = L.out[l];
+      h.a_k = 1;
+      h.B = p16 + L.w_off[l];
+      h.b_k = 1;
+      h.b_n = L.out[l];
+      h.mask = w.act[l - 1];
+      h.C16 = w.dz[1 - cur];
+      LEARN_CUDA(gemm(h, s), "MLP input gradient");
+      cur = 1 - cur;
+    }
+  }
+  LEARN_CUDA(cudaGetLastError(), "MLP backward");
+  return LSP_OK;
+}
+
+lsp_status lsp_mlp_adamw(int64_t n, float* params, uint16_t* params_bf16, const float* grad, float* m,
+                         float* v, int64_t step, float lr, float beta1, float beta2, float eps,
+                         float weight_decay, lsp_stream_t stream) {
+  if (n < 1 || !params || !params_bf16 || !grad || !m || !v || step < 1) return err_arg("bad argument");
+  const float bc1 = 1.0f - powf(beta1, (float)step), bc2 = 1.0f - powf(beta2, (float)step);
+  adamw_kernel<<<1024, 256, 0, (cudaStream_t)stream>>>(n, params, (bf16*)params_bf16, grad, m, v, lr, beta1,
+                                                       beta2, eps, weight_decay, bc1, bc2);
+  LEARN_CUDA(cudaGetLastError(), "AdamW");
+  return LSP_OK;
+}
+
+lsp_status lsp_to_bf16(const float* a, uint16_t* b, int64_t n, lsp_stream_t stream) {
+  if (n < 0 || (n > 0 && (!a || !b))) return err_arg("bad argument");
+  if (n == 0) return LSP_OK;
+  to_bf16_kernel<<<1024, 256, 0, (cudaStream_t)stream>>>(n, a, (bf16*)b);
+  LEARN_CUDA(cudaGetLastError(), "to_bf16");
+  return LSP_OK;
+}
+
+lsp_status lsp_top_classes(const float* logits, int64_t rows, int32_t n_classes, int32_t k,
+                           int32_t* classes, lsp_stream_t stream) {
+  if (rows < 0 || n_classes < 1 || k < 1 || k > 16 || k > n_classes) return err_arg("bad argument");
+  if (rows == 0) return LSP_OK;
+  if (!logits || !classes) return err_arg("NULL argument");
+  topk_kernel<<<(unsigned)((rows + 127) / 128), 128, 0, (cudaStream_t)stream>>>(logits, rows, n_classes,
+                                                                                 k, classes);
+  LEARN_CUDA(cudaGetLastError(), "top classes");
+  return LSP_OK;
+}
+
+}  // extern "C"
+
+// The refine entry point needs the library's prologue and main kernel; it
+// lives here with its own workspace layout.
+namespace {
+struct RefineLayout {
+  size_t off_obj, off_rec, off_state, off_best, off_full, off_win, off_list, off_cnt, total;
+  int n_chunks;
+};
+constexpr int kRefineK = 8;          // reseed interval of the refine kernel
+constexpr int kRefineThreads = 128;  // 128 threads x 16 frequencies = 2048 bins per item
+
+void refine_layout(int64_t n_obj, int64_t total_nt, int64_t n_f, RefineLayout* r) {
+  size_t off = 0;
+  auto take = [&](size_t b) {
+    size_t at = off;
+    off = align256(off + b);
+    return at;
+  };
+  const int64_t chunk = (int64_t)kRefineThreads * 2 * kRefineK;
+  r->n_chunks = (int)((n_f + chunk - 1) / chunk);
+  r->off_obj = take((size_t)n_obj * sizeof(ObjInfo));
+  r->off_rec = take((size_t)total_nt * sizeof(RecF32));
+  r->off_state = take((size_t)n_obj * sizeof(RefineState));
+  r->off_best = take((size_t)n_obj * sizeof(ChunkBest));
+  r->off_full = take((size_t)n_obj * r->n_chunks * sizeof(ChunkBest));
+  r->off_win = take((size_t)n_obj * sizeof(int32_t));
+  r->off_list = take((size_t)n_obj * sizeof(int32_t));
+  r->off_cnt = take(64);
+  r->total = off;
+}
+}  // namespace
+
+extern "C" {
+
+lsp_status lsp_refine_workspace_size(int64_t n_obj, int64_t total_nt, const lsp_grid* grid, size_t* bytes) {
+  if (!bytes || !grid || n_obj < 0 || total_nt < 0 || grid->n_f < 1) return err_arg("bad argument");
+  RefineLayout r;
+  refine_layout(n_obj, total_nt, grid->n_f, &r);
+  *bytes = r.total;
+  return LSP_OK;
+}
+
+lsp_status lsp_refine_windows(const double* t, const float* y, const int64_t* offsets, int64_t n_obj,
+                              int64_t total_nt, const lsp_grid* grid, int32_t norm, const int32_t* classes,
+                              int32_t k_windows, int64_t window, int64_t stride, float stop_power,
+                              float fallback_power, int32_t inconclusive_fallback, lsp_peak* peaks,
+                              int32_t* info, void* workspace, size_t ws_bytes, lsp_stream_t stream) {
+  if (!grid || !(grid->f_min > 0.0) || !(grid->f_max > grid->f_min) || grid->n_f < 1)
+    return err_arg("bad grid");
+  if (n_obj < 0 || n_obj > INT32_MAX || total_nt < 0) return err_arg("bad n_obj or total_nt");
+  if (n_obj == 0) return LSP_OK;
+  if (!t || !y || !offsets || !classes || !peaks) return err_arg("NULL argument");
+  if (k_windows < 1 || k_windows > 64) return err_arg("k_windows must be 1..64");
+  const int64_t chunk = (int64_t)kRefineThreads * 2 * kRefineK;
+  if (window < 1 || window > chunk) return err_arg("window must be 1..2048");
+  if (stride < 1) return err_arg("stride must be >= 1");
+  RefineLayout r;
+  refine_layout(n_obj, total_nt, grid->n_f, &r);
+  if (!workspace || ws_bytes < r.total || ((uintptr_t)workspace) % 256)
+    return err_arg("refine workspace too small or misaligned");
+  cudaStream_t s = (cudaStream_t)stream;
+  char* ws = (char*)workspace;
+  ObjInfo* obj = (ObjInfo*)(ws + r.off_obj);
+  RecF32* rec = (RecF32*)(ws + r.off_rec);
+  RefineState* state = (RefineState*)(ws + r.off_state);
+  ChunkBest* best = (ChunkBest*)(ws + r.off_best);
+  ChunkBest* full = (ChunkBest*)(ws + r.off_full);
+  int32_t* win = (int32_t*)(ws + r.off_win);
+  int32_t* list = (int32_t*)(ws + r.off_list);
+  uint32_t* cnt = (uint32_t*)(ws + r.off_cnt);  // [0] list count, [1] items, [2] queue
+  const double df = (grid->f_max - grid->f_min) / (double)grid->n_f;
+  int n_sm = 152, dev = 0;
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+  int bps = main_blocks_per_sm(0, 1, kRefineK, 2 * kRefineK, kRefineThreads, 0);
+  if (bps < 1) bps = 1;
+
+  LEARN_CUDA(launch_stats(t, y, false, offsets, n_obj, total_nt, 1, norm, obj, s), "refine prologue");
+  LEARN_CUDA(launch_records(t, y, false, obj, n_obj, total_nt, grid->f_min, df, false, rec, s),
+             "refine records");
+  const unsigned g1 = (unsigned)((n_obj + 255) / 256);
+  refine_init<<<g1, 256, 0, s>>>(n_obj, obj, state);
+  MainLaunch ml;
+  ml.prec = 0;
+  ml.packed = 1;
+  ml.k_reseed = kRefineK;
+  ml.fpt = 2 * kRefineK;
+  ml.threads = kRefineThreads;
+  ml.top = 0;
+  ml.rec = rec;
+  ml.obj = obj;
+  ml.order = list;
+  ml.power_out = nullptr;
+  ml.part = nullptr;
+  ml.cand = nullptr;
+  ml.queue = cnt + 2;
+  ml.n_f = grid->n_f;
+  ml.split = 1;
+  for (int rr = 0; rr < k_windows; ++rr) {
+    LEARN_CUDA(cudaMemsetAsync(cnt, 0, 16, s), "refine counters");
+    refine_list<<<g1, 256, 0, s>>>(n_obj, rr, k_windows, classes, stride, window, grid->n_f, state, win,
+                                    list, cnt);
+    items_from_count<<<1, 1, 0, s>>>(cnt, 1u, cnt + 1);
+    ml.best = best;
+    ml.n_chunks = 1;
+    ml.n_items = n_obj;  // upper bound; the kernel reads the count
+    ml.n_items_dev = cnt + 1;
+    ml.win_start = win;
+    ml.win_len = (int32_t)window;
+    ml.grid = (int)(n_sm * bps);
+    LEARN_CUDA(launch_main(ml, s), "refine main kernel");
+    refine_merge<<<g1, 256, 0, s>>>(n_obj, rr, k_windows, stop_power, best, state);
+  }
+  // full-grid fallback for the objects whose refined peak stayed weak
+  LEARN_CUDA(cudaMemsetAsync(cnt, 0, 16, s), "fallback counters");
+  fallback_list<<<g1, 256, 0, s>>>(n_obj, fallback_power, inconclusive_fallback, obj, state, list, cnt);
+  items_from_count<<<1, 1, 0, s>>>(cnt, (uint32_t)r.n_chunks, cnt + 1);
+  ml.best = full;
+  ml.n_chunks = r.n_chunks;
+  ml.n_items = n_obj * (int64_t)r.n_chunks;
+  ml.n_items_dev = cnt + 1;
+  ml.win_start = nullptr;
+  ml.win_len = 0;
+  ml.grid = (int)(n_sm * bps);
+  LEARN_CUDA(launch_main(ml, s), "fallback main kernel");
+  refine_finalize<<<g1, 256, 0, s>>>(n_obj, obj, state, fallback_power, inconclusive_fallback, full,
+                                     r.n_chunks, grid->f_min, df, peaks, info);
+  LEARN_CUDA(cudaGetLastError(), "refine finalize");
+  return LSP_OK;
+}
+
+}  // extern "C"

@@ -68,6 +68,9 @@ cudaError_t launch_main_f32(const MainLaunch& ml, cudaStream_t stream) {
   p.n_chunks = ml.n_chunks;
   p.split = ml.split;
   p.n_items = ml.n_items;
+  p.n_items_dev = ml.n_items_dev;
+  p.win_start = ml.win_start;
+  p.win_len = ml.win_len;
   cudaError_t err = cudaErrorInvalidValue;
   dispatch_f32(ml.packed, ml.k_reseed, [&](auto kern) { err = launch_kernel(kern, ml, p, stream); });
   return err;

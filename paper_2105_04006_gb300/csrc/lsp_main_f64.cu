@@ -45,6 +45,9 @@ cudaError_t launch_main_f64(const MainLaunch& ml, cudaStream_t stream) {
   p.n_chunks = ml.n_chunks;
   p.split = ml.split;
   p.n_items = ml.n_items;
+  p.n_items_dev = ml.n_items_dev;
+  p.win_start = ml.win_start;
+  p.win_len = ml.win_len;
   cudaError_t err = cudaErrorInvalidValue;
   size_t dyn = main_dyn_smem(1, ml.fpt, ml.threads, ml.top);
   dispatch_f64(ml.k_reseed, [&](auto kern) {

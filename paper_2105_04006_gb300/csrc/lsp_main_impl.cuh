@@ -142,7 +142,7 @@ __global__ void __launch_bounds__(256) main_f32_packed(MainParams<RecF32, float>
   extern __shared__ __align__(16) unsigned char dyn_smem[];
   float* s_pw = reinterpret_cast<float*>(dyn_smem);
   const int tid = threadIdx.x;
-  const uint32_t n_items = (uint32_t)p.n_items;
+  const uint32_t n_items = p.n_items_dev ? *p.n_items_dev : (uint32_t)p.n_items;
   const uint32_t split = (uint32_t)p.split, n_chunks = (uint32_t)p.n_chunks;
 
   for (;;) {
@@ -157,7 +157,9 @@ __global__ void __launch_bounds__(256) main_f32_packed(MainParams<RecF32, float>
     const uint32_t orank = oc / n_chunks;
     const int64_t o = p.order ? (int64_t)p.order[orank] : (int64_t)orank;
     const ObjInfo oi = p.obj[o];
-    const int64_t kc0 = (int64_t)chunk * blockDim.x * F;
+    const int64_t kc0 = p.win_start ? (int64_t)p.win_start[o] : (int64_t)chunk * blockDim.x * F;
+    // bins of this item lie in [kc0, kend): the grid, or the object's window
+    const int64_t kend = p.win_start ? (kc0 + p.win_len < p.n_f ? kc0 + p.win_len : p.n_f) : p.n_f;
     const uint32_t k0 = (uint32_t)(kc0 + (int64_t)tid * F);
     const uint32_t k1 = k0 + K;
     const int64_t ob = oi.begin + (int64_t)oi.n * is / split;
@@ -199,14 +201,14 @@ __global__ void __launch_bounds__(256) main_f32_packed(MainParams<RecF32, float>
         bool ill0, ill1;
         pv[m] = scale * lsp_power_f32(a0, b0, c0, d0, nf, ill0);
         pv[K + m] = scale * lsp_power_f32(a1, b1, c1, d1, nf, ill1);
-        if (ill0 && (int64_t)k0 + m < p.n_f) bad |= 1u << m;
-        if (ill1 && (int64_t)k1 + m < p.n_f) bad |= 1u << (K + m);
+        if (ill0 && (int64_t)k0 + m < kend) bad |= 1u << m;
+        if (ill1 && (int64_t)k1 + m < kend) bad |= 1u << (K + m);
       }
       if (oi.flags) bad = 0u;
       fix_ill_conditioned<F>(pv, bad, k0, p.rec, oi.begin, oi.n, oi.norm_scale);
-      if (p.power_out) store_row<F>(p.power_out + o * p.n_f, (int64_t)k0, pv, p.n_f);
+      if (p.power_out) store_row<F>(p.power_out + o * p.n_f, (int64_t)k0, pv, kend);
       const int64_t res = o * (int64_t)n_chunks + chunk;
-      chunk_results_f32<F>(pv, k0, kc0, p.n_f, p.best + res, p.cand ? p.cand + res : nullptr, s_pw, red);
+      chunk_results_f32<F>(pv, k0, kc0, kend, p.best + res, p.cand ? p.cand + res : nullptr, s_pw, red);
     } else {
       float* part = p.part + (int64_t)is * p.n_f * 4;
 #pragma unroll
