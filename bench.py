@@ -40,6 +40,7 @@ import synth  # noqa: E402
 METRIC = "objects/sec and trig-sum evals/s (N_t*N_f) vs FP32 roofline; learned vs plain"
 FP32_OPS_PER_PAIR = 8      # 2 FMUL + 2 FFMA (rotation) + 4 FFMA (XC, XS, CC, CS)
 FP32_LANES_PER_SM = 128    # FP32 lanes per SM per clock
+FP64_LANES_PER_SM = 2      # FP64 FMAs per SM per clock: 1.25 TFLOP/s nominal / (2 x 152 SMs x 2.07 GHz)
 
 WORKLOADS = {
     "ragged_survey": dict(kind="batch", top_k=1, power=False, cpu_sample=64, ref_per_step=6,
@@ -246,11 +247,14 @@ def run_gpu(args, w, name):
 
     b = make_workload(name, rank, args.n_obj)
     g = lsp.Grid(b.grid.f_min, b.grid.f_max, b.grid.n_f)
+    fp64 = args.precision == "fp64"
+    ydt = np.float64 if fp64 else np.float32
     t = torch.tensor(b.t, dtype=torch.float64, device=dev)
-    y = torch.tensor(b.y.astype(np.float32), device=dev)
+    y = torch.tensor(b.y.astype(ydt), device=dev)
     off = torch.tensor(b.offsets, dtype=torch.int64, device=dev) if b.n_obj > 1 else None
-    power = torch.empty((b.n_obj, g.n_f), dtype=torch.float32, device=dev) if w["power"] else None
-    plan = lsp.Plan(b.n_obj, b.t.size, g, top_k=w["top_k"])
+    power = (torch.empty((b.n_obj, g.n_f), dtype=torch.float64 if fp64 else torch.float32, device=dev)
+             if w["power"] else None)
+    plan = lsp.Plan(b.n_obj, b.t.size, g, top_k=w["top_k"], precision=args.precision)
     if args.config:
         keys = ("k_reseed", "freqs_per_thread", "block_threads", "obs_split", "packed")
         plan.set_config(**dict(zip(keys, (int(v) for v in args.config.split(",")))))
@@ -296,9 +300,10 @@ def run_gpu(args, w, name):
 
     # end to end through the host-buffer entry point (pinned host memory)
     th = torch.from_numpy(b.t).pin_memory()
-    yh = torch.from_numpy(b.y.astype(np.float32)).pin_memory()
+    yh = torch.from_numpy(b.y.astype(ydt)).pin_memory()
     oh = torch.from_numpy(b.offsets).pin_memory() if b.n_obj > 1 else None
-    ph = torch.empty((b.n_obj, g.n_f), dtype=torch.float32).pin_memory() if w["power"] else None
+    ph = (torch.empty((b.n_obj, g.n_f), dtype=torch.float64 if fp64 else torch.float32).pin_memory()
+          if w["power"] else None)
     pk_host = np.empty(b.n_obj * w["top_k"], dtype=lsp.PEAK_DTYPE)
     plan.enable_timing(False)
     plan.execute_host(th, yh, oh, power=ph, peaks=pk_host)  # warm: allocates staging, captures
@@ -316,15 +321,17 @@ def run_gpu(args, w, name):
     if dist is not None:
         dist.all_reduce(e2e_s, op=dist.ReduceOp.MAX)
     e2e_value = world * b.n_obj * args.steps / float(e2e_s.item())
-    h2d = th.numel() * 8 + yh.numel() * 4 + (oh.numel() * 8 if oh is not None else 0)
-    d2h = pk_host.nbytes + (ph.numel() * 4 if ph is not None else 0)
+    ysz = 8 if fp64 else 4
+    h2d = th.numel() * 8 + yh.numel() * ysz + (oh.numel() * 8 if oh is not None else 0)
+    d2h = pk_host.nbytes + (ph.numel() * ysz if ph is not None else 0)
 
     n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
     main_avg = statistics.mean(main_ms)
     achieved = pairs / (main_avg / 1e3) / 1e9
     clk_mhz = (clocks or {}).get("sm_mhz") or 0.0
-    peak = n_sm * FP32_LANES_PER_SM * clk_mhz * 1e6 / FP32_OPS_PER_PAIR / 1e9 if clk_mhz else None
-    peak_max = n_sm * FP32_LANES_PER_SM * 2070e6 / FP32_OPS_PER_PAIR / 1e9
+    lanes = FP64_LANES_PER_SM if fp64 else FP32_LANES_PER_SM
+    peak = n_sm * lanes * clk_mhz * 1e6 / FP32_OPS_PER_PAIR / 1e9 if clk_mhz else None
+    peak_max = n_sm * lanes * 2070e6 / FP32_OPS_PER_PAIR / 1e9
     src = source_hash()
     traffic = recorded_traffic(name, src)
 
@@ -334,17 +341,18 @@ def run_gpu(args, w, name):
         line = {
             "impl": "gb300", "metric": METRIC, "value": value, "unit": "objects/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": statistics.mean(step_ms),
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64" if fp64 else "f32",
             "data": "synthetic",
             "config": {"workload": name, "shape": w["desc"], "n_obj": b.n_obj, "total_nt": int(b.t.size),
-                       "n_f": g.n_f, "precision": "fp32 sums, fp64/fixed-point phase",
+                       "n_f": g.n_f,
+                       "precision": "fp64" if fp64 else "fp32 sums, fp64/fixed-point phase",
                        "l2": "flushed between steps (256 MiB write)", "kernel_config": plan.config},
             "pairs_per_s": world * pairs * args.steps / total_s,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gpair/s",
                          "frac": (achieved / peak) if peak else None, "traffic": traffic,
                          "kernel": "main trig-sum kernel", "main_kernel_ms": main_avg,
-                         "peak_basis": f"{n_sm} SMs x {FP32_LANES_PER_SM} FP32 lanes x sampled SM clock "
-                                       f"/ {FP32_OPS_PER_PAIR} FP32 ops per pair",
+                         "peak_basis": f"{n_sm} SMs x {lanes} {'FP64' if fp64 else 'FP32'} lanes x sampled SM "
+                                       f"clock / {FP32_OPS_PER_PAIR} ops per pair",
                          "peak_at_max_clock": peak_max, "source_hash": src},
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": "objects/s", "h2d_bytes_per_step": int(h2d),
@@ -361,15 +369,91 @@ def run_gpu(args, w, name):
     return 0
 
 
+# ------------------------------------------------------------ learned vs plain
+def run_learned(args):
+    """Learned proposal + refine against the plain full grid on the same batch."""
+    import torch
+    import paper_2105_04006_gb300 as lsp
+    from paper_2105_04006_gb300 import learned as L
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    prop = None
+    if args.checkpoint and os.path.exists(args.checkpoint):
+        prop, _ = L.Proposer.load(args.checkpoint, dev)
+        trained_on = f"checkpoint {os.path.basename(args.checkpoint)}"
+    else:
+        per, sets = 25_000, []
+        for part in range((args.n_train + per - 1) // per):
+            sets.append(L.labelled_set(min(per, args.n_train - part * per), dev, "learned_train", part))
+        prop = L.Proposer(sets[0]["grid"].n_f, dev, seed=1)
+        L.train(prop, sets, epochs=10, batch_size=1024, lr=2e-3)
+        del sets
+        trained_on = f"{args.n_train} learned_train curves labelled by lsp_batch, 10 epochs"
+        if args.checkpoint:
+            prop.save(args.checkpoint)
+    n_obj = args.n_obj or 100_000
+    test = L.labelled_set(n_obj, dev, "learned_infer", 1000 + rank)
+    b, g = test["batch"], test["grid"]
+    plan = lsp.Plan(b.n_obj, b.t.size, g)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def timed(fn):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        ms = []
+        for i in range(args.steps):
+            flush.fill_(i & 0xFF)
+            a, c = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            fn()
+            c.record()
+            c.synchronize()
+            ms.append(a.elapsed_time(c))
+        return statistics.mean(ms)
+
+    clk = ClockSampler(os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[0])
+    clk.start()
+    clk.mark(0)
+    ms_plain = timed(lambda: plan.execute(test["t"], test["y"], test["off"]))
+    ms_learned = timed(lambda: L.propose_and_refine(prop, test["t"], test["y"], test["off"], g))
+    clk.mark(1)
+    clocks = clk.stop()
+    ev = L.evaluate(prop, test)
+    line = {
+        "impl": "gb300", "metric": METRIC, "value": b.n_obj / (ms_learned / 1e3), "unit": "objects/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_learned,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "learned", "shape": f"{b.n_obj} objects, N_t~U{{50..500}}, N_f=1e5, "
+                                                   "8 windows of 2048, fallback < 0.3",
+                   "trained_on": trained_on, "stop_power": prop.stop_power,
+                   "l2": "flushed between steps (256 MiB write)"},
+        "plain": {"value": b.n_obj / (ms_plain / 1e3), "ms_per_step": ms_plain},
+        "speedup_vs_plain": ms_plain / ms_learned,
+        "recovery": ev["recovery"], "fallback_fraction": ev["fallback"],
+        "mean_windows": ev["mean_windows"], "pair_fraction": ev["pair_fraction"],
+        "clocks": clocks,
+    }
+    plan.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="ragged_survey")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["learned"], default="ragged_survey")
+    ap.add_argument("--n-train", type=int, default=1_000_000, help="learned workload: training curves")
+    ap.add_argument("--checkpoint", default=None, help="learned workload: proposer checkpoint to load/save")
     ap.add_argument("--no-tune", action="store_true", help="use the default kernel configuration")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
+    ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
     ap.add_argument("--config", default=None,
                     help="force a kernel configuration: k_reseed,freqs_per_thread,block_threads,obs_split,packed")
     ap.add_argument("--n-obj", type=int, default=None,
@@ -377,6 +461,11 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
+    if args.workload == "learned":
+        if args.impl == "reference":
+            print(json.dumps({"impl": "reference", "unavailable": "the learned stage has no CPU reference arm"}))
+            return 0
+        return run_learned(args)
     w = WORKLOADS[args.workload]
     if args.impl == "reference":
         return run_reference(args, w, args.workload)

@@ -8,8 +8,9 @@ The arithmetic lives in ``lsp_oracle.c`` (plain C, FP64, libm, OpenMP): Eq. 1
 (tau) and Eq. 2 (power) of Section 2, evaluated in two scans per frequency,
 with the half-open grid of Section 2, the first-maximum argmax of Section 3.3,
 and the lsp-c parallel schedules of Section 4.5.  This module only marshals
-numpy arrays through ctypes.  ``mlp`` and ``features`` hold the oracle of the
-learned-proposal stage.
+numpy arrays through ctypes.  ``gls_batch`` is the generalized periodogram of
+Section 4.11 (weighted three-parameter least squares); ``oracle.learned``
+holds the oracle of the learned-proposal stage.
 """
 from __future__ import annotations
 
@@ -62,6 +63,8 @@ def _load():
             lib.oracle_top_local_maxima.argtypes = [P, i64, i32, P, P]
             lib.oracle_top_local_maxima.restype = i32
             lib.oracle_num_threads.restype = i32
+            lib.oracle_gls_batch.argtypes = [P, P, P, P, i64, d, d, i64, i32, P, P, P, P]
+            lib.oracle_gls_batch.restype = i32
             _lib = lib
     return _lib
 
@@ -132,6 +135,28 @@ def lsp_batch(t, y, offsets, f_min, f_max, n_f, *, norm=1, center=True, top_k=1,
                              int(norm), int(bool(center)), top_k, _ptr(power), _ptr(arg_idx),
                              _ptr(arg_pow), _ptr(top_idx), _ptr(top_pow), _ptr(flags))
     res = dict(arg_idx=arg_idx, arg_pow=arg_pow, top_idx=top_idx, top_pow=top_pow, flags=flags)
+    if return_power:
+        res["power"] = power
+    return res
+
+
+def gls_batch(t, y, dy, offsets, f_min, f_max, n_f, *, norm=1, return_power=True):
+    """Generalized periodogram (Section 4.11): weighted 3-parameter least squares.
+
+    ``dy`` None means unit weights.  Returns a dict with ``power`` (if
+    requested), ``arg_idx``, ``arg_pow`` and ``flags``.
+    """
+    t, y = _f64(t), _f64(y)
+    dyv = None if dy is None else _f64(dy)
+    off = np.ascontiguousarray(offsets, dtype=np.int64)
+    n_obj = off.size - 1
+    power = np.empty((n_obj, n_f), dtype=np.float64) if return_power else None
+    arg_idx = np.empty(n_obj, dtype=np.int64)
+    arg_pow = np.empty(n_obj, dtype=np.float64)
+    flags = np.empty(n_obj, dtype=np.int32)
+    _load().oracle_gls_batch(_ptr(t), _ptr(y), _ptr(dyv), _ptr(off), n_obj, float(f_min), float(f_max), int(n_f),
+                             int(norm), _ptr(power), _ptr(arg_idx), _ptr(arg_pow), _ptr(flags))
+    res = dict(arg_idx=arg_idx, arg_pow=arg_pow, flags=flags)
     if return_power:
         res["power"] = power
     return res

@@ -301,3 +301,109 @@ int oracle_lsp_single_ld(const double* t, const double* y, int64_t n_t, double f
   }
   return 0;
 }
+
+/*
+ * Generalized L-S periodogram (Section 4.11: photometric errors and a
+ * floating mean).  The paper gives no formula; its plain definition is used:
+ * at each frequency the weighted least-squares fit of
+ *     y(t) ~ a cos(w t) + b sin(w t) + c,   weights 1 / dy^2,
+ * and the power
+ *     P = 1 - chi2_min(w) / chi2_0,   chi2_0 = sum_j w_j (y_j - ybar_w)^2,
+ * the fraction of the weighted variance the sinusoid explains (in [0, 1]).
+ * norm = 0 returns (chi2_0 - chi2_min) / 2 instead, the generalized
+ * counterpart of Eq. 2's P.  The 3x3 normal equations are solved by Gaussian
+ * elimination with partial pivoting in FP64.  dy NULL means unit weights.
+ * Objects with fewer than three observations, zero weighted variance or a
+ * non-positive / non-finite error get power 0 and a flag.
+ */
+static double gls_power(const double* ts, const double* y, const double* w, int64_t n, double f,
+                        double chi2_0, int norm) {
+  double wv = ORACLE_TWO_PI * f;
+  double m[3][4] = {{0}};
+  double syy = 0.0;
+  for (int64_t j = 0; j < n; ++j) {
+    double phi[3] = {cos(wv * ts[j]), sin(wv * ts[j]), 1.0};
+    for (int r = 0; r < 3; ++r) {
+      for (int c = 0; c < 3; ++c) m[r][c] += w[j] * phi[r] * phi[c];
+      m[r][3] += w[j] * phi[r] * y[j];
+    }
+    syy += w[j] * y[j] * y[j];
+  }
+  double rhs[3] = {m[0][3], m[1][3], m[2][3]};
+  for (int col = 0; col < 3; ++col) {
+    int piv = col;
+    for (int r = col + 1; r < 3; ++r)
+      if (fabs(m[r][col]) > fabs(m[piv][col])) piv = r;
+    if (fabs(m[piv][col]) <= 1e-300) return 0.0;
+    if (piv != col)
+      for (int c = 0; c < 4; ++c) {
+        double tmp = m[col][c];
+        m[col][c] = m[piv][c];
+        m[piv][c] = tmp;
+      }
+    for (int r = col + 1; r < 3; ++r) {
+      double fct = m[r][col] / m[col][col];
+      for (int c = col; c < 4; ++c) m[r][c] -= fct * m[col][c];
+    }
+  }
+  double beta[3];
+  for (int r = 2; r >= 0; --r) {
+    double acc = m[r][3];
+    for (int c = r + 1; c < 3; ++c) acc -= m[r][c] * beta[c];
+    beta[r] = acc / m[r][r];
+  }
+  double chi2_min = syy;
+  for (int r = 0; r < 3; ++r) chi2_min -= beta[r] * rhs[r];
+  double red = chi2_0 - chi2_min;
+  return norm ? red / chi2_0 : 0.5 * red;
+}
+
+static int prepare_gls(const double* t, const double* y, const double* dy, int64_t n, double* ts,
+                       double* w, double* chi2_0) {
+  int flags = 0;
+  *chi2_0 = 0.0;
+  if (n < 3) flags |= ORACLE_FLAG_FEW_OBS;
+  for (int64_t j = 0; j < n; ++j) {
+    double e = dy ? dy[j] : 1.0;
+    if (!isfinite(t[j]) || !isfinite(y[j]) || !isfinite(e) || !(e > 0.0)) flags |= ORACLE_FLAG_NONFINITE;
+  }
+  if (n == 0 || (flags & ORACLE_FLAG_NONFINITE)) return flags;
+  double tmin = t[0], sw = 0.0, swy = 0.0;
+  for (int64_t j = 0; j < n; ++j) {
+    if (t[j] < tmin) tmin = t[j];
+    double e = dy ? dy[j] : 1.0;
+    w[j] = 1.0 / (e * e);
+    sw += w[j];
+    swy += w[j] * y[j];
+  }
+  double ybar = swy / sw;
+  for (int64_t j = 0; j < n; ++j) {
+    ts[j] = t[j] - tmin;
+    *chi2_0 += w[j] * (y[j] - ybar) * (y[j] - ybar);
+  }
+  if (!(*chi2_0 > 0.0)) flags |= ORACLE_FLAG_ZERO_VAR;
+  return flags;
+}
+
+int oracle_gls_batch(const double* t, const double* y, const double* dy, const int64_t* offsets,
+                     int64_t n_obj, double f_min, double f_max, int64_t n_f, int norm, double* power,
+                     int64_t* arg_idx, double* arg_pow, int32_t* flags_out) {
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int64_t o = 0; o < n_obj; ++o) {
+    int64_t b = offsets[o], n = offsets[o + 1] - offsets[o];
+    double* pg = power ? power + o * n_f : (double*)malloc(sizeof(double) * (size_t)n_f);
+    double* ts = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    double* w = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    double chi2_0 = 0.0;
+    int fl = prepare_gls(t + b, y + b, dy ? dy + b : NULL, n, ts, w, &chi2_0);
+    for (int64_t k = 0; k < n_f; ++k)
+      pg[k] = fl ? 0.0 : gls_power(ts, y + b, w, n, grid_freq(f_min, f_max, n_f, k), chi2_0, norm);
+    arg_idx[o] = fl ? -1 : oracle_argmax(pg, n_f);
+    arg_pow[o] = fl ? 0.0 : pg[arg_idx[o]];
+    if (flags_out) flags_out[o] = fl;
+    free(ts);
+    free(w);
+    if (!power) free(pg);
+  }
+  return 0;
+}

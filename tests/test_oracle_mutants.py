@@ -32,6 +32,15 @@ MUTANTS = {
     "cos_sin_swapped": ("xc += x[j] * c;", "xc += x[j] * s;"),
 }
 
+# mutants of the generalized periodogram and the check that must catch them
+GLS_MUTANTS = {
+    "gls_no_offset_column": ("double phi[3] = {cos(wv * ts[j]), sin(wv * ts[j]), 1.0};",
+                             "double phi[3] = {cos(wv * ts[j]), sin(wv * ts[j]), 0.0};"),
+    "gls_weight_not_squared": ("w[j] = 1.0 / (e * e);", "w[j] = 1.0 / e;"),
+    "gls_unweighted_mean": ("double ybar = swy / sw;", "double ybar = swy / (double)n;"),
+    "gls_wrong_normalisation": ("return norm ? red / chi2_0 : 0.5 * red;", "return norm ? red / syy : 0.5 * red;"),
+}
+
 
 def _compile(tmp_path, name, old, new):
     src = open(SRC).read()
@@ -107,3 +116,42 @@ def test_mutant_is_caught(tmp_path, name):
     old, new = MUTANTS[name]
     lib = _compile(str(tmp_path), name, old, new)
     assert not _pins_hold(lib), f"mutant {name} survived the pins"
+
+
+def _gls_holds(lib) -> bool:
+    P, d, i64, i32 = ctypes.c_void_p, ctypes.c_double, ctypes.c_int64, ctypes.c_int
+    lib.oracle_gls_batch.argtypes = [P, P, P, P, i64, d, d, i64, i32, P, P, P, P]
+    g = np.random.default_rng(8)
+    ok = True
+    for n in (6, 15):
+        t = np.sort(g.uniform(60000, 60030, n))
+        y = g.normal(0, 1, n) + 2.0
+        dy = g.uniform(0.05, 0.5, n)
+        off = np.array([0, n], dtype=np.int64)
+        out = np.empty(20)
+        ai, ap, fl = np.empty(1, np.int64), np.empty(1), np.empty(1, np.int32)
+        lib.oracle_gls_batch(t.ctypes.data, y.ctypes.data, dy.ctypes.data, off.ctypes.data, 1, 0.3, 4.0, 20, 1,
+                             out.ctypes.data, ai.ctypes.data, ap.ctypes.data, fl.ctypes.data)
+        fk = 0.3 + np.arange(20) * (3.7 / 20)
+        w = 1 / dy ** 2
+        for k in (0, 7, 19):
+            wt = 2 * math.pi * fk[k]
+            X = np.stack([np.cos(wt * (t - t[0])), np.sin(wt * (t - t[0])), np.ones(n)], axis=1)
+            beta, *_ = np.linalg.lstsq(X * np.sqrt(w)[:, None], y * np.sqrt(w), rcond=None)
+            chi2 = np.sum(w * (y - X @ beta) ** 2)
+            chi0 = np.sum(w * (y - np.sum(w * y) / np.sum(w)) ** 2)
+            ok &= abs(out[k] - (1 - chi2 / chi0)) <= 1e-8
+    return bool(ok)
+
+
+def test_gls_unmutated_passes(tmp_path):
+    lib = _compile(str(tmp_path), "gls_identity", "int oracle_version(void) { return 1; }",
+                   "int oracle_version(void) { return 1; }")
+    assert _gls_holds(lib)
+
+
+@pytest.mark.parametrize("name", sorted(GLS_MUTANTS))
+def test_gls_mutant_is_caught(tmp_path, name):
+    old, new = GLS_MUTANTS[name]
+    lib = _compile(str(tmp_path), name, old, new)
+    assert not _gls_holds(lib), f"mutant {name} survived the pins"

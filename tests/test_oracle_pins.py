@@ -196,3 +196,80 @@ def test_batch_equals_singles_and_flags(oracle_mod):
     assert res["flags"][9] & oracle_mod.FLAG_NONFINITE
     assert (res["arg_idx"][6:] == -1).all()
     assert (res["power"][6:] == 0).all()
+
+
+# ---------------------------------------------- generalized periodogram (Section 4.11)
+def _wlsq_power(t, y, dy, f):
+    """Fraction of the weighted variance explained by a cos + b sin + c (numpy lstsq)."""
+    w = 1.0 / dy ** 2
+    sw = np.sqrt(w)
+    wt = 2 * math.pi * f
+    X = np.stack([np.cos(wt * t), np.sin(wt * t), np.ones_like(t)], axis=1)
+    beta, *_ = np.linalg.lstsq(X * sw[:, None], y * sw, rcond=None)
+    chi2 = np.sum(w * (y - X @ beta) ** 2)
+    ybar = np.sum(w * y) / np.sum(w)
+    chi0 = np.sum(w * (y - ybar) ** 2)
+    return 1.0 - chi2 / chi0
+
+
+@pytest.mark.parametrize("n_t", [4, 7, 12, 40])
+def test_gls_weighted_least_squares(oracle_mod, n_t):
+    g = np.random.default_rng(200 + n_t)
+    t = np.sort(g.uniform(60000, 60030, n_t))
+    y = g.normal(0, 1, n_t)
+    dy = g.uniform(0.05, 0.5, n_t)
+    res = oracle_mod.gls_batch(t, y, dy, [0, n_t], 0.3, 4.0, 37)
+    fk = oracle_mod.grid_freqs(0.3, 4.0, 37)
+    ref = np.array([_wlsq_power(t - t[0], y, dy, f) for f in fk])
+    np.testing.assert_allclose(res["power"][0], ref, rtol=1e-8, atol=1e-10)
+    # the non-normalised form is half the chi-square reduction
+    res0 = oracle_mod.gls_batch(t, y, dy, [0, n_t], 0.3, 4.0, 37, norm=0)
+    w = 1 / dy ** 2
+    chi0 = np.sum(w * (y - np.sum(w * y) / np.sum(w)) ** 2)
+    np.testing.assert_allclose(res0["power"][0], 0.5 * chi0 * ref, rtol=1e-8, atol=1e-10)
+
+
+def test_gls_exact_fit_and_bounds(oracle_mod):
+    g = np.random.default_rng(21)
+    t = np.sort(g.uniform(60000, 61000, 80))
+    k0, f_min, f_max, n_f = 123, 0.1, 5.0, 500
+    f0 = oracle_mod.grid_freqs(f_min, f_max, n_f)[k0]
+    y = 0.4 * np.cos(2 * math.pi * f0 * t + 1.1) + 3.0
+    dy = g.uniform(0.01, 0.3, 80)
+    res = oracle_mod.gls_batch(t, y, dy, [0, 80], f_min, f_max, n_f)
+    assert abs(res["power"][0, k0] - 1.0) < 1e-9
+    yn = y + g.normal(0, 0.2, 80)
+    p = oracle_mod.gls_batch(t, yn, dy, [0, 80], f_min, f_max, n_f)["power"][0]
+    assert p.min() >= -1e-12 and p.max() <= 1 + 1e-12
+
+
+def test_gls_unit_weights_fourier_frequencies_equal_fft(oracle_mod):
+    # at Fourier frequencies of even sampling, cos/sin are orthogonal to the
+    # constant, so the floating mean changes nothing: P = 2 |DFT_m|^2 / (N sum yc^2)
+    n, dt = 48, 0.25
+    g = np.random.default_rng(22)
+    t = 60000.0 + dt * np.arange(n)
+    y = g.normal(0, 1, n) + 5.0
+    df = 1.0 / (n * dt)
+    n_f = n // 2 - 1
+    p = oracle_mod.gls_batch(t, y, None, [0, n], df, df * (n_f + 1), n_f)["power"][0]
+    yc = y - y.mean()
+    ref = 2 * np.abs(np.fft.fft(yc)[1:n_f + 1]) ** 2 / (n * np.dot(yc, yc))
+    np.testing.assert_allclose(p, ref, rtol=1e-9, atol=1e-12)
+
+
+def test_gls_invariances_and_flags(oracle_mod):
+    g = np.random.default_rng(23)
+    t = np.sort(g.uniform(60000, 60500, 60))
+    y = np.sin(2 * math.pi * 1.3 * t) + g.normal(0, 0.3, 60)
+    dy = g.uniform(0.1, 0.4, 60)
+    args = ([0, 60], 0.2, 6.0, 800)
+    base = oracle_mod.gls_batch(t, y, dy, *args)["power"][0]
+    for tt, yy, ee in [(t + 777.7, y, dy), (t, -2.0 * y + 9.0, dy), (t, y, 3.0 * dy)]:
+        np.testing.assert_allclose(oracle_mod.gls_batch(tt, yy, ee, *args)["power"][0], base, atol=1e-8)
+    off = np.array([0, 2, 5, 8], dtype=np.int64)
+    tt = np.array([0.0, 1.0, 0.0, 1.0, 2.0, 0.0, 1.0, 2.0]) + 60000
+    yy = np.array([1.0, 2.0, 1.0, 1.0, 1.0, 1.0, 2.0, 3.0])
+    ee = np.array([1.0, 1.0, 1.0, 1.0, 1.0, 1.0, -1.0, 1.0])
+    fl = oracle_mod.gls_batch(tt, yy, ee, off, 0.2, 6.0, 10)["flags"]
+    assert fl[0] & oracle_mod.FLAG_FEW_OBS and fl[1] & oracle_mod.FLAG_ZERO_VAR and fl[2] & oracle_mod.FLAG_NONFINITE
