@@ -178,6 +178,29 @@ lsp_status lsp_batch_noalloc(const double* t, const void* y, const int64_t* offs
                              void* power_out, lsp_peak* peaks, lsp_stream_t stream);
 
 /*
+ * Generalized periodogram (Section 4.11: photometric errors, floating
+ * mean).  The paper ports Astropy's implementation without giving a
+ * formula; this library computes, at each grid frequency, the weighted
+ * least-squares fit y ~ a cos(wt) + b sin(wt) + c with weights 1/dy^2 and
+ * the power P = 1 - chi2_min(w) / chi2_0 (chi2_0 about the weighted mean) for
+ * LSP_NORM_STANDARD, or (chi2_0 - chi2_min)/2 for LSP_NORM_PSD.  dy has y's
+ * type and layout (NULL: unit weights).  Objects need at least three
+ * observations; a non-positive or non-finite dy flags LSP_FLAG_NONFINITE.
+ * Arguments otherwise as lsp_batch / lsp_periodogram; the workspace size
+ * comes from lsp_workspace_size_gls.  There is no split-N_t for a single
+ * object here.
+ */
+lsp_status lsp_workspace_size_gls(int64_t n_obj, int64_t total_nt, const lsp_grid* grid,
+                                  const lsp_opts* opts, size_t* bytes);
+lsp_status lsp_batch_gls(const double* t, const void* y, const void* dy, const int64_t* offsets,
+                         int64_t n_obj, int64_t total_nt, const lsp_grid* grid, const lsp_opts* opts,
+                         void* power_out, lsp_peak* peaks, void* workspace, size_t ws_bytes,
+                         lsp_stream_t stream);
+lsp_status lsp_periodogram_gls(const double* t, const void* y, const void* dy, int64_t n_t,
+                               const lsp_grid* grid, const lsp_opts* opts, void* power_out,
+                               lsp_peak* peaks, void* workspace, size_t ws_bytes, lsp_stream_t stream);
+
+/*
  * Period of stored periodograms (Section 3.3's separate argmax step):
  * power is n_obj x n_f of type float (LSP_FP32) or double (LSP_FP64); each
  * row's first maximum is written to peaks[o] (idx, power, freq, period;

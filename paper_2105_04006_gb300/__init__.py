@@ -80,7 +80,7 @@ EXPORTS = [
     "lsp_batch_noalloc", "lsp_grid_for_span",
     "lsp_mlp_param_count", "lsp_mlp_workspace_size", "lsp_featurize", "lsp_mlp_forward",
     "lsp_mlp_loss_grad", "lsp_mlp_adamw", "lsp_to_bf16", "lsp_top_classes", "lsp_refine_workspace_size",
-    "lsp_refine_windows",
+    "lsp_refine_windows", "lsp_batch_gls", "lsp_periodogram_gls", "lsp_workspace_size_gls",
 ]
 
 
@@ -111,6 +111,9 @@ def lib():
             L.lsp_batch.argtypes = [P, P, P, i64, i64, GP, OP, P, P, P, sz, P]
             L.lsp_argmax_period.argtypes = [P, i64, i64, GP, i32, P, P]
             L.lsp_batch_noalloc.argtypes = [P, P, P, i64, i64, GP, OP, P, P, P]
+            L.lsp_batch_gls.argtypes = [P, P, P, P, i64, i64, GP, OP, P, P, P, sz, P]
+            L.lsp_workspace_size_gls.argtypes = [i64, i64, GP, OP, ctypes.POINTER(sz)]
+            L.lsp_periodogram_gls.argtypes = [P, P, P, i64, GP, OP, P, P, P, sz, P]
             L.lsp_grid_for_span.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_double, GP]
             L.lsp_plan_create.argtypes = [ctypes.POINTER(P), i64, i64, GP, OP]
             L.lsp_plan_execute.argtypes = [P, P, P, P, P, P, P]
@@ -257,6 +260,38 @@ def batch(t, y, offsets, grid: Grid, *, return_power=False, workspace=None, **kw
     _check(lib().lsp_batch(_ptr(t), _ptr(y), _ptr(offsets), n_obj, total, ctypes.byref(grid),
                            ctypes.byref(opts), _ptr(power), _ptr(peaks), _ptr(ws), ws.numel(),
                            _stream_handle(t.device)))
+    return power, peaks
+
+
+def workspace_size_gls(n_obj, total_nt, grid: Grid, opts: Opts) -> int:
+    n = ctypes.c_size_t(0)
+    _check(lib().lsp_workspace_size_gls(int(n_obj), int(total_nt), ctypes.byref(grid), ctypes.byref(opts),
+                                        ctypes.byref(n)))
+    return int(n.value)
+
+
+def batch_gls(t, y, dy, offsets, grid: Grid, *, return_power=False, workspace=None, **kw):
+    """Generalized periodogram of a CSR batch (photometric errors dy, floating mean).
+
+    dy: tensor like y, or None for unit weights.  Returns (power or None, peaks).
+    """
+    torch = _torch()
+    opts = make_opts(**kw)
+    _require(t, "t", torch.float64)
+    _require(y, "y", _dtypes(opts), t.device)
+    if dy is not None:
+        _require(dy, "dy", _dtypes(opts), t.device)
+    _require(offsets, "offsets", torch.int64, t.device)
+    n_obj = offsets.numel() - 1
+    ws_bytes = workspace_size_gls(n_obj, t.numel(), grid, opts)
+    ws = workspace if workspace is not None else torch.empty(max(ws_bytes, 256), dtype=torch.uint8,
+                                                                device=t.device)
+    power = (torch.empty((n_obj, grid.n_f), dtype=_dtypes(opts), device=t.device)
+             if return_power else None)
+    peaks = torch.empty(max(n_obj, 0) * opts.top_k * 40, dtype=torch.uint8, device=t.device)
+    _check(lib().lsp_batch_gls(_ptr(t), _ptr(y), _ptr(dy), _ptr(offsets), n_obj, t.numel(), ctypes.byref(grid),
+                               ctypes.byref(opts), _ptr(power), _ptr(peaks), _ptr(ws), ws.numel(),
+                               _stream_handle(t.device)))
     return power, peaks
 
 

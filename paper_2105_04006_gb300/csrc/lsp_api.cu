@@ -64,7 +64,7 @@ int current_sm_count() {
 
 // Resolved configuration and workspace layout of one call.
 struct Layout {
-  int prec, packed, k, fpt, threads, split, top_k, top, norm, center;
+  int prec, packed, k, fpt, threads, split, top_k, top, norm, center, gls;
   int64_t n_obj, total_nt, n_f;
   double f_min, df;
   int32_t n_chunks, n_res_chunks;
@@ -89,7 +89,7 @@ lsp_status check_grid(const lsp_grid* g) {
 }
 
 lsp_status resolve(int64_t n_obj, int64_t total_nt, const lsp_grid* g, const lsp_opts* opts_in,
-                   const lsp_config* cfg, Layout* L) {
+                   const lsp_config* cfg, Layout* L, bool gls = false) {
   lsp_status st = check_grid(g);
   if (st) return st;
   if (n_obj < 0 || n_obj > INT32_MAX) return fail(LSP_E_ARG, "n_obj out of range");
@@ -114,6 +114,7 @@ lsp_status resolve(int64_t n_obj, int64_t total_nt, const lsp_grid* g, const lsp
   l.n_f = g->n_f;
   l.f_min = g->f_min;
   l.df = (g->f_max - g->f_min) / (double)g->n_f;
+  l.gls = gls ? 1 : 0;
 
   int k, fpt, threads, packed, split_req;
   if (cfg) {
@@ -123,7 +124,8 @@ lsp_status resolve(int64_t n_obj, int64_t total_nt, const lsp_grid* g, const lsp
     packed = cfg->packed;
     split_req = cfg->obs_split;
   } else {
-    k = o.k_reseed ? o.k_reseed : 8;
+    // generalized kernels keep six sums per frequency: shorter FP32 chains
+    k = o.k_reseed ? o.k_reseed : ((gls && l.prec == LSP_FP32) ? 4 : 8);
     if (l.prec == LSP_FP64) {
       fpt = o.freqs_per_thread ? o.freqs_per_thread : k;
       threads = o.block_threads ? o.block_threads : 128;
@@ -138,9 +140,9 @@ lsp_status resolve(int64_t n_obj, int64_t total_nt, const lsp_grid* g, const lsp
   }
   if (threads < 64 || threads > 256 || threads % 32)
     return fail(LSP_E_ARG, "block_threads must be a multiple of 32 in [64, 256]");
-  if (!main_variant_exists(l.prec, packed, k, fpt))
-    return fail(LSP_E_UNSUPPORTED, "no kernel for precision %d with k_reseed=%d, freqs_per_thread=%d",
-                l.prec, k, fpt);
+  if (!main_variant_exists(l.prec, packed, k, fpt, l.gls))
+    return fail(LSP_E_UNSUPPORTED, "no %skernel for precision %d with k_reseed=%d, freqs_per_thread=%d",
+                gls ? "generalized " : "", l.prec, k, fpt);
   l.k = k;
   l.fpt = fpt;
   l.threads = threads;
@@ -149,7 +151,7 @@ lsp_status resolve(int64_t n_obj, int64_t total_nt, const lsp_grid* g, const lsp
   const int64_t chunk = (int64_t)threads * fpt;
   l.n_chunks = (int32_t)((l.n_f + chunk - 1) / chunk);
   int split = 1;
-  if (n_obj == 1) {
+  if (n_obj == 1 && !gls) {  // the generalized kernels have no split-N_t combine
     if (split_req > 0) {
       split = split_req;
     } else {
@@ -184,7 +186,7 @@ lsp_status resolve(int64_t n_obj, int64_t total_nt, const lsp_grid* g, const lsp
   l.off_part = take(split > 1 ? (size_t)split * l.n_f * 4 * (l.prec ? 8 : 4) : 0);
   l.total = off;
 
-  int bps = main_blocks_per_sm(l.prec, l.packed, l.k, l.fpt, l.threads, l.top);
+  int bps = main_blocks_per_sm(l.prec, l.packed, l.k, l.fpt, l.threads, l.top, l.gls);
   if (bps <= 0) {
     cudaGetLastError();
     bps = 1;
@@ -198,7 +200,8 @@ lsp_status resolve(int64_t n_obj, int64_t total_nt, const lsp_grid* g, const lsp
 // The launch sequence of one periodogram call (stream-ordered, no syncs).
 lsp_status run(const Layout& L, const double* t, const void* y, const int64_t* offsets,
                void* power_out, lsp_peak* peaks, char* ws, cudaStream_t st,
-               cudaEvent_t ev_main0 = nullptr, cudaEvent_t ev_main1 = nullptr) {
+               cudaEvent_t ev_main0 = nullptr, cudaEvent_t ev_main1 = nullptr,
+               const void* dy = nullptr) {
   if (L.n_obj == 0) return LSP_OK;
   ObjInfo* obj = (ObjInfo*)(ws + L.off_obj);
   void* rec = ws + L.off_rec;
@@ -210,10 +213,10 @@ lsp_status run(const Layout& L, const double* t, const void* y, const int64_t* o
   void* part = L.split > 1 ? (void*)(ws + L.off_part) : nullptr;
   const bool y64 = L.prec == LSP_FP64;
 
-  LSP_CUDA(launch_stats(t, y, y64, offsets, L.n_obj, L.total_nt, L.center,
-                        L.norm, obj, st),
+  LSP_CUDA(launch_stats(t, y, y64, offsets, L.n_obj, L.total_nt, L.center, L.norm, obj, st, L.gls != 0,
+                        dy),
            "prologue (statistics)");
-  LSP_CUDA(launch_records(t, y, y64, obj, L.n_obj, L.total_nt, L.f_min, L.df, y64, rec, st),
+  LSP_CUDA(launch_records(t, y, y64, obj, L.n_obj, L.total_nt, L.f_min, L.df, y64, rec, st, L.gls != 0, dy),
            "prologue (records)");
   if (order) LSP_CUDA(launch_lpt_order(obj, L.n_obj, hist, order, st), "work-queue order");
   LSP_CUDA(cudaMemsetAsync(queue, 0, 16, st), "queue reset");
@@ -222,6 +225,7 @@ lsp_status run(const Layout& L, const double* t, const void* y, const int64_t* o
   ml.packed = L.packed;
   ml.k_reseed = L.k;
   ml.fpt = L.fpt;
+  ml.gls = L.gls;
   ml.threads = L.threads;
   ml.grid = L.grid;
   ml.top = L.top && L.split == 1;
@@ -350,6 +354,43 @@ lsp_status lsp_batch(const double* t, const void* y, const int64_t* offsets, int
   if ((st = check_io(total_nt, t, y))) return st;
   if ((st = check_ws(L, workspace, ws_bytes))) return st;
   return run(L, t, y, offsets, power_out, peaks, (char*)workspace, (cudaStream_t)stream);
+}
+
+lsp_status lsp_workspace_size_gls(int64_t n_obj, int64_t total_nt, const lsp_grid* grid,
+                                  const lsp_opts* opts, size_t* bytes) {
+  if (!bytes) return fail(LSP_E_ARG, "bytes is NULL");
+  Layout L;
+  lsp_status st = resolve(n_obj, total_nt, grid, opts, nullptr, &L, true);
+  if (st) return st;
+  *bytes = L.total;
+  return LSP_OK;
+}
+
+lsp_status lsp_batch_gls(const double* t, const void* y, const void* dy, const int64_t* offsets,
+                         int64_t n_obj, int64_t total_nt, const lsp_grid* grid, const lsp_opts* opts,
+                         void* power_out, lsp_peak* peaks, void* workspace, size_t ws_bytes,
+                         lsp_stream_t stream) {
+  g_err.clear();
+  Layout L;
+  lsp_status st = resolve(n_obj, total_nt, grid, opts, nullptr, &L, true);
+  if (st) return st;
+  if (n_obj == 0) return LSP_OK;
+  if (!offsets) return fail(LSP_E_ARG, "offsets must not be NULL");
+  if ((st = check_io(total_nt, t, y))) return st;
+  if ((st = check_ws(L, workspace, ws_bytes))) return st;
+  return run(L, t, y, offsets, power_out, peaks, (char*)workspace, (cudaStream_t)stream, nullptr, nullptr, dy);
+}
+
+lsp_status lsp_periodogram_gls(const double* t, const void* y, const void* dy, int64_t n_t,
+                               const lsp_grid* grid, const lsp_opts* opts, void* power_out,
+                               lsp_peak* peaks, void* workspace, size_t ws_bytes, lsp_stream_t stream) {
+  g_err.clear();
+  Layout L;
+  lsp_status st = resolve(1, n_t, grid, opts, nullptr, &L, true);
+  if (st) return st;
+  if ((st = check_io(n_t, t, y))) return st;
+  if ((st = check_ws(L, workspace, ws_bytes))) return st;
+  return run(L, t, y, nullptr, power_out, peaks, (char*)workspace, (cudaStream_t)stream, nullptr, nullptr, dy);
 }
 
 lsp_status lsp_argmax_period(const void* power, int64_t n_obj, int64_t n_f, const lsp_grid* grid,

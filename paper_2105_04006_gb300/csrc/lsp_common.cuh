@@ -28,10 +28,15 @@ struct __align__(16) ObjInfo {
   int64_t begin;     // offsets[o]
   int32_t n;         // N_t (0 for an object with bad offsets)
   int32_t flags;     // LSP_FLAG_*
-  double norm_scale; // 2 / sum_y2 (standard normalisation) or 1 (PSD)
+  double norm_scale; // 2 / sum_y2 (standard normalisation) or 1 (PSD); generalized: 1 or sum_y2 / 2
   float norm_scale_f; // the same, rounded to FP32 (the FP32 kernels never touch FP64)
-  int32_t pad[3];
+  float wsum_f;       // generalized periodogram: sum of the weights 1/dy^2 (FP32)
+  double wsum;        // the same in FP64
 };
+
+// Generalized periodogram (Section 4.11): the records hold u = w (y - ybar_w)
+// in the y slot and the weight w = 1/dy^2 in the spare word (pad / pad bits),
+// with ybar_w the weighted mean; ObjInfo.sum_y2 is then sum w (y - ybar_w)^2.
 
 // FP32 path record, 32 bytes.  Phase of frequency k at this observation, in
 // cycles, is frac(a + k b) with a = f_min (t - t0) and b = df (t - t0), both
@@ -225,6 +230,76 @@ static __device__ __noinline__ double exact_power_warp(const RecF32* __restrict_
   cc = warp_sum_d(cc);
   cs = warp_sum_d(cs);
   return norm_scale * lsp_power<double>(xc, xs, cc, cs, (double)n, EpsRel<double>::v);
+}
+
+// ---------------------------------------- generalized periodogram (Section 4.11)
+// Power of the weighted fit y ~ a cos + b sin + c from the six weighted sums
+// (y centred on its weighted mean, u = w y'):  YC = sum u c, YS = sum u s,
+// C = sum w c, S = sum w s, CCw = sum w c^2, CSw = sum w c s; W = sum w and
+// YY = sum w y'^2 per object.  Eliminating the offset c,
+//   CC = CCw - C^2/W,  SS = (W - CCw) - S^2/W,  CS = CSw - C S / W,
+//   D = CC SS - CS^2,  P = (SS YC^2 + CC YS^2 - 2 CS YC YS) / (YY D),
+// the fraction of the weighted variance the sinusoid explains.  `ill`
+// reports a Gram determinant D below 5 % of its largest value W^2/4.
+template <typename Real>
+__device__ __forceinline__ Real gls_power(Real yc, Real ys, Real c, Real s, Real ccw, Real csw, Real w,
+                                          Real yy, Real eps_rel, bool& ill) {
+  const Real iw = Real(1) / w;
+  const Real cc = ccw - c * c * iw;
+  const Real ss = (w - ccw) - s * s * iw;
+  const Real cs = csw - c * s * iw;
+  const Real d = cc * ss - cs * cs;
+  ill = d < Real(0.0125) * w * w;
+  if (!(d > eps_rel * w * w) || !(yy > Real(0))) return Real(0);
+  const Real num = ss * yc * yc + cc * ys * ys - Real(2) * cs * yc * ys;
+  return (num > Real(0) ? num : Real(0)) / (yy * d);
+}
+
+// FP64 re-evaluation of a generalized bin by the whole warp (exact phases).
+static __device__ __noinline__ double exact_gls_power_warp(const RecF32* __restrict__ rec, int64_t begin,
+                                                           int n, uint32_t k, double wsum, double yy,
+                                                           double norm_scale) {
+  double xc = 0.0, xs = 0.0, c1 = 0.0, s1 = 0.0, cc = 0.0, cs = 0.0;
+  for (int j = threadIdx.x & 31; j < n; j += 32) {
+    const RecF32 r = rec[begin + j];
+    const uint64_t a = ((uint64_t)r.a_hi << 32) | r.a_lo;
+    const uint64_t b = ((uint64_t)r.b_hi << 32) | r.b_lo;
+    double c, s;
+    seed_sincos_f64(a + (uint64_t)k * b, c, s);
+    const double u = (double)r.y, w = (double)__uint_as_float(r.pad);
+    xc = fma(u, c, xc);
+    xs = fma(u, s, xs);
+    c1 = fma(w, c, c1);
+    s1 = fma(w, s, s1);
+    cc = fma(w * c, c, cc);
+    cs = fma(w * c, s, cs);
+  }
+  xc = warp_sum_d(xc);
+  xs = warp_sum_d(xs);
+  c1 = warp_sum_d(c1);
+  s1 = warp_sum_d(s1);
+  cc = warp_sum_d(cc);
+  cs = warp_sum_d(cs);
+  bool ill;
+  return norm_scale * gls_power<double>(xc, xs, c1, s1, cc, cs, wsum, yy, EpsRel<double>::v, ill);
+}
+
+template <int F>
+__device__ __forceinline__ void fix_ill_conditioned_gls(float (&pv)[F], uint32_t bad, uint32_t k0,
+                                                        const RecF32* __restrict__ rec, const ObjInfo& oi) {
+  if (!__any_sync(0xffffffffu, bad != 0u)) return;
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int m = 0; m < F; ++m) {
+    unsigned mask = __ballot_sync(0xffffffffu, (bad >> m) & 1u);
+    while (mask) {
+      const int l = __ffs(mask) - 1;
+      mask &= mask - 1;
+      const uint32_t k = __shfl_sync(0xffffffffu, k0 + (uint32_t)m, l);
+      const double p = exact_gls_power_warp(rec, oi.begin, oi.n, k, oi.wsum, oi.sum_y2, oi.norm_scale);
+      if (lane == l) pv[m] = (float)p;
+    }
+  }
 }
 
 // Replace the ill-conditioned bins (bit m of `bad`: bin k0 + m) of every lane

@@ -13,12 +13,15 @@ namespace lsp {
 
 // Prologue, Section 2 (zero-mean magnitudes) and the per-observation phase
 // data of the rotation recurrence.  y is float (y64 = false) or double.
+// gls: weighted statistics / records of the generalized periodogram (dy
+// NULL: unit weights).
 cudaError_t launch_stats(const double* t, const void* y, bool y64, const int64_t* offsets,
                          int64_t n_obj, int64_t total_nt, int center, int norm, ObjInfo* obj,
-                         cudaStream_t stream);
+                         cudaStream_t stream, bool gls = false, const void* dy = nullptr);
 cudaError_t launch_records(const double* t, const void* y, bool y64, const ObjInfo* obj,
                            int64_t n_obj, int64_t max_nt_single, double f_min, double df,
-                           bool rec64, void* rec, cudaStream_t stream);
+                           bool rec64, void* rec, cudaStream_t stream, bool gls = false,
+                           const void* dy = nullptr);
 // Objects ordered by decreasing N_t (counting sort).
 cudaError_t launch_lpt_order(const ObjInfo* obj, int64_t n_obj, uint32_t* hist, int32_t* order,
                              cudaStream_t stream);
@@ -29,6 +32,7 @@ struct MainLaunch {
   int packed;    // FP32 only
   int k_reseed;  // chain length K
   int fpt;       // frequencies per thread (packed: 2K; scalar: K)
+  int gls = 0;   // generalized periodogram kernels
   int threads;
   int grid;      // persistent CTAs
   int top;       // 1: top-k candidates
@@ -48,10 +52,10 @@ struct MainLaunch {
   const int32_t* win_start = nullptr;     // per-object window origins (packed FP32 kernels)
   int32_t win_len = 0;
 };
-bool main_variant_exists(int prec, int packed, int k_reseed, int fpt);
+bool main_variant_exists(int prec, int packed, int k_reseed, int fpt, int gls = 0);
 cudaError_t launch_main(const MainLaunch& ml, cudaStream_t stream);
 // CTAs of the main variant resident per SM (0 if the variant does not exist).
-int main_blocks_per_sm(int prec, int packed, int k_reseed, int fpt, int threads, int top);
+int main_blocks_per_sm(int prec, int packed, int k_reseed, int fpt, int threads, int top, int gls = 0);
 size_t main_dyn_smem(int prec, int fpt, int threads, int top);
 
 // Split-N_t combine (single object): sums the partial sums in a fixed order,

@@ -25,7 +25,15 @@ int occupancy(Kern kern, int threads, size_t dyn) {
 }
 
 template <typename Fn>
-bool dispatch_f32(int packed, int k, Fn&& fn) {
+bool dispatch_f32(int packed, int k, int gls, Fn&& fn) {
+  if (gls) {
+    if (!packed) return false;
+    switch (k) {
+      case 4: fn(main_f32_packed_gls<4>); return true;
+      case 8: fn(main_f32_packed_gls<8>); return true;
+    }
+    return false;
+  }
   if (packed) {
     switch (k) {
       case 4: fn(main_f32_packed<4>); return true;
@@ -42,15 +50,15 @@ bool dispatch_f32(int packed, int k, Fn&& fn) {
 }
 }  // namespace
 
-bool main_variant_exists_f32(int packed, int k, int fpt) {
+bool main_variant_exists_f32(int packed, int k, int fpt, int gls) {
   if (fpt != (packed ? 2 * k : k)) return false;
-  return dispatch_f32(packed, k, [](auto) {});
+  return dispatch_f32(packed, k, gls, [](auto) {});
 }
 
-int main_blocks_per_sm_f32(int packed, int k, int fpt, int threads, int top) {
+int main_blocks_per_sm_f32(int packed, int k, int fpt, int threads, int top, int gls) {
   int nb = 0;
   size_t dyn = main_dyn_smem(0, fpt, threads, top);
-  dispatch_f32(packed, k, [&](auto kern) { nb = occupancy(kern, threads, dyn); });
+  dispatch_f32(packed, k, gls, [&](auto kern) { nb = occupancy(kern, threads, dyn); });
   return nb;
 }
 
@@ -72,7 +80,7 @@ cudaError_t launch_main_f32(const MainLaunch& ml, cudaStream_t stream) {
   p.win_start = ml.win_start;
   p.win_len = ml.win_len;
   cudaError_t err = cudaErrorInvalidValue;
-  dispatch_f32(ml.packed, ml.k_reseed, [&](auto kern) { err = launch_kernel(kern, ml, p, stream); });
+  dispatch_f32(ml.packed, ml.k_reseed, ml.gls, [&](auto kern) { err = launch_kernel(kern, ml, p, stream); });
   return err;
 }
 

@@ -6,7 +6,14 @@ namespace lsp {
 
 namespace {
 template <typename Fn>
-bool dispatch_f64(int k, Fn&& fn) {
+bool dispatch_f64(int k, int gls, Fn&& fn) {
+  if (gls) {
+    switch (k) {
+      case 4: fn(main_f64_gls<4>); return true;
+      case 8: fn(main_f64_gls<8>); return true;
+    }
+    return false;
+  }
   switch (k) {
     case 4: fn(main_scalar<double, RecF64, 4>); return true;
     case 8: fn(main_scalar<double, RecF64, 8>); return true;
@@ -16,15 +23,15 @@ bool dispatch_f64(int k, Fn&& fn) {
 }
 }  // namespace
 
-bool main_variant_exists_f64(int k, int fpt) {
+bool main_variant_exists_f64(int k, int fpt, int gls) {
   if (fpt != k) return false;
-  return dispatch_f64(k, [](auto) {});
+  return dispatch_f64(k, gls, [](auto) {});
 }
 
-int main_blocks_per_sm_f64(int k, int fpt, int threads, int top) {
+int main_blocks_per_sm_f64(int k, int fpt, int threads, int top, int gls) {
   int nb = 0;
   size_t dyn = main_dyn_smem(1, fpt, threads, top);
-  dispatch_f64(k, [&](auto kern) {
+  dispatch_f64(k, gls, [&](auto kern) {
     if (dyn > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, threads, dyn) != cudaSuccess) nb = 0;
   });
@@ -50,7 +57,7 @@ cudaError_t launch_main_f64(const MainLaunch& ml, cudaStream_t stream) {
   p.win_len = ml.win_len;
   cudaError_t err = cudaErrorInvalidValue;
   size_t dyn = main_dyn_smem(1, ml.fpt, ml.threads, ml.top);
-  dispatch_f64(ml.k_reseed, [&](auto kern) {
+  dispatch_f64(ml.k_reseed, ml.gls, [&](auto kern) {
     if (dyn > 48 * 1024) {
       err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
       if (err != cudaSuccess) return;

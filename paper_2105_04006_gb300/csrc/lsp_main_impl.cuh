@@ -226,6 +226,179 @@ __global__ void __launch_bounds__(256) main_f32_packed(MainParams<RecF32, float>
 }
 
 // ------------------------------------------------------------------------
+// Generalized periodogram (Section 4.11), FP32, two packed reseed chains:
+// the same tiling and seeding as main_f32_packed with six weighted sums per
+// frequency (11 FP32 operations per pair instead of 8).  Records carry
+// u = w (y - ybar_w) in the y word and w in the spare word.
+template <int K>
+__global__ void __launch_bounds__(256) main_f32_packed_gls(MainParams<RecF32, float> p) {
+  constexpr int F = 2 * K;
+  __shared__ uint4 s_obs[2 * LSP_TILE_OBS];
+  __shared__ unsigned long long red[32];
+  __shared__ uint32_t s_item;
+  extern __shared__ __align__(16) unsigned char dyn_smem[];
+  float* s_pw = reinterpret_cast<float*>(dyn_smem);
+  const int tid = threadIdx.x;
+  const uint32_t n_items = p.n_items_dev ? *p.n_items_dev : (uint32_t)p.n_items;
+  const uint32_t n_chunks = (uint32_t)p.n_chunks;
+
+  for (;;) {
+    if (tid == 0) s_item = atomicAdd(p.queue, 1u);
+    __syncthreads();
+    const uint32_t item = s_item;
+    __syncthreads();
+    if (item >= n_items) break;
+    const uint32_t chunk = item % n_chunks;
+    const uint32_t orank = item / n_chunks;
+    const int64_t o = p.order ? (int64_t)p.order[orank] : (int64_t)orank;
+    const ObjInfo oi = p.obj[o];
+    const int64_t kc0 = (int64_t)chunk * blockDim.x * F;
+    const uint32_t k0 = (uint32_t)(kc0 + (int64_t)tid * F);
+    const uint32_t k1 = k0 + K;
+    const int64_t ob = oi.begin;
+    const int64_t oe = oi.flags ? ob : oi.begin + oi.n;
+
+    f2_t xc[K], xs[K], cw[K], sw[K], cc[K], cs[K];
+#pragma unroll
+    for (int m = 0; m < K; ++m) xc[m] = xs[m] = cw[m] = sw[m] = cc[m] = cs[m] = 0ull;
+
+    for (int64_t ts = ob; ts < oe; ts += LSP_TILE_OBS) {
+      const int nt = (int)((oe - ts) < LSP_TILE_OBS ? (oe - ts) : LSP_TILE_OBS);
+      const uint4* src = reinterpret_cast<const uint4*>(p.rec + ts);
+      for (int i = tid; i < 2 * nt; i += blockDim.x) s_obs[i] = __ldg(src + i);
+      __syncthreads();
+      for (int j = 0; j < nt; ++j) {
+        const uint4 r0 = s_obs[2 * j];
+        const uint4 r1 = s_obs[2 * j + 1];
+        f2_t c2, s2;
+        seed_pair(make_uint4(r0.w, r1.x, r1.y, 0u), k0, k1, c2, s2);
+        const f2_t u2 = f2_of(r0.x, r0.x), w2 = f2_of(r1.w, r1.w);
+        const f2_t cr2 = f2_of(r0.y, r0.y), sr2 = f2_of(r0.z, r0.z);
+        const uint32_t nsr = r0.z ^ 0x80000000u;
+        const f2_t nsr2 = f2_of(nsr, nsr);
+#pragma unroll
+        for (int m = 0; m < K; ++m) {
+          xc[m] = f2_fma(u2, c2, xc[m]);
+          xs[m] = f2_fma(u2, s2, xs[m]);
+          cw[m] = f2_fma(w2, c2, cw[m]);
+          sw[m] = f2_fma(w2, s2, sw[m]);
+          const f2_t wc = f2_mul(w2, c2);
+          cc[m] = f2_fma(wc, c2, cc[m]);
+          cs[m] = f2_fma(wc, s2, cs[m]);
+          if (m + 1 < K) {
+            const f2_t tc = f2_mul(c2, cr2);
+            const f2_t tsr = f2_mul(s2, cr2);
+            const f2_t cn = f2_fma(s2, nsr2, tc);
+            s2 = f2_fma(c2, sr2, tsr);
+            c2 = cn;
+          }
+        }
+      }
+      __syncthreads();
+    }
+
+    float pv[F];
+    const float scale = oi.norm_scale_f, wsum = oi.wsum_f, yy = (float)oi.sum_y2;
+    uint32_t bad = 0u;
+#pragma unroll
+    for (int m = 0; m < K; ++m) {
+      float v[2][6];
+      f2_unpack(xc[m], v[0][0], v[1][0]);
+      f2_unpack(xs[m], v[0][1], v[1][1]);
+      f2_unpack(cw[m], v[0][2], v[1][2]);
+      f2_unpack(sw[m], v[0][3], v[1][3]);
+      f2_unpack(cc[m], v[0][4], v[1][4]);
+      f2_unpack(cs[m], v[0][5], v[1][5]);
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        bool ill;
+        const float pw = gls_power<float>(v[h][0], v[h][1], v[h][2], v[h][3], v[h][4], v[h][5], wsum, yy,
+                                          EpsRel<float>::v, ill);
+        const int idx = h * K + m;
+        pv[idx] = scale * pw;
+        if (ill && (int64_t)k0 + idx < p.n_f) bad |= 1u << idx;
+      }
+    }
+    if (oi.flags) bad = 0u;
+    fix_ill_conditioned_gls<F>(pv, bad, k0, p.rec, oi);
+    if (p.power_out) store_row<F>(p.power_out + o * p.n_f, (int64_t)k0, pv, p.n_f);
+    const int64_t res = o * (int64_t)n_chunks + chunk;
+    chunk_results_f32<F>(pv, k0, kc0, p.n_f, p.best + res, p.cand ? p.cand + res : nullptr, s_pw, red);
+  }
+}
+
+// Generalized periodogram, FP64 scalar chains (one chain of K per thread).
+template <int K>
+__global__ void __launch_bounds__(256) main_f64_gls(MainParams<RecF64, double> p) {
+  constexpr int F = K;
+  __shared__ uint4 s_rec[3 * LSP_TILE_OBS];
+  __shared__ double red_p[32];
+  __shared__ int64_t red_k[32];
+  __shared__ uint32_t s_item;
+  extern __shared__ __align__(16) unsigned char dyn_smem[];
+  double* s_pw = reinterpret_cast<double*>(dyn_smem);
+  const int tid = threadIdx.x;
+  const RecF64* srec = reinterpret_cast<const RecF64*>(s_rec);
+  for (;;) {
+    if (tid == 0) s_item = atomicAdd(p.queue, 1u);
+    __syncthreads();
+    const int64_t item = s_item;
+    __syncthreads();
+    if (item >= p.n_items) break;
+    const int chunk = (int)(item % p.n_chunks);
+    const int64_t orank = item / p.n_chunks;
+    const int64_t o = p.order ? (int64_t)p.order[orank] : orank;
+    const ObjInfo oi = p.obj[o];
+    const int64_t kc0 = (int64_t)chunk * blockDim.x * F;
+    const uint32_t k0 = (uint32_t)(kc0 + (int64_t)tid * F);
+    const int64_t ob = oi.begin;
+    const int64_t oe = oi.flags ? ob : oi.begin + oi.n;
+    double xc[K], xs[K], cw[K], sw[K], cc[K], cs[K];
+#pragma unroll
+    for (int m = 0; m < K; ++m) xc[m] = xs[m] = cw[m] = sw[m] = cc[m] = cs[m] = 0.0;
+    for (int64_t ts = ob; ts < oe; ts += LSP_TILE_OBS) {
+      const int nt = (int)((oe - ts) < LSP_TILE_OBS ? (oe - ts) : LSP_TILE_OBS);
+      const uint4* src = reinterpret_cast<const uint4*>(p.rec + ts);
+      for (int i = tid; i < 3 * nt; i += blockDim.x) s_rec[i] = __ldg(src + i);
+      __syncthreads();
+      for (int j = 0; j < nt; ++j) {
+        const RecF64 r = srec[j];
+        double c, s;
+        seed_sincos_f64(r.a + (uint64_t)k0 * r.b, c, s);
+        const double u = r.y, w = __longlong_as_double((long long)r.pad), cr = r.cr, sr = r.sr;
+#pragma unroll
+        for (int m = 0; m < K; ++m) {
+          xc[m] = fma(u, c, xc[m]);
+          xs[m] = fma(u, s, xs[m]);
+          cw[m] = fma(w, c, cw[m]);
+          sw[m] = fma(w, s, sw[m]);
+          const double wc = w * c;
+          cc[m] = fma(wc, c, cc[m]);
+          cs[m] = fma(wc, s, cs[m]);
+          if (m + 1 < K) {
+            const double cn = fma(-s, sr, c * cr);
+            s = fma(c, sr, s * cr);
+            c = cn;
+          }
+        }
+      }
+      __syncthreads();
+    }
+    double pv[F];
+#pragma unroll
+    for (int m = 0; m < K; ++m) {
+      bool ill;
+      pv[m] = oi.norm_scale * gls_power<double>(xc[m], xs[m], cw[m], sw[m], cc[m], cs[m], oi.wsum, oi.sum_y2,
+                                                EpsRel<double>::v, ill);
+    }
+    if (p.power_out) store_row<F>(p.power_out + o * p.n_f, (int64_t)k0, pv, p.n_f);
+    const int64_t res = o * p.n_chunks + chunk;
+    chunk_results<double, F>(pv, (int64_t)k0, kc0, p.n_f, p.best + res, p.cand ? p.cand + res : nullptr, s_pw,
+                             red_p, red_k);
+  }
+}
+
+// ------------------------------------------------------------------------
 // Scalar kernel: one reseed chain of K frequencies per thread.  Real = float
 // (FP32 records, SFU seeds) or double (FP64 records, FP64 sincospi seeds).
 template <typename Real, typename Rec, int K>

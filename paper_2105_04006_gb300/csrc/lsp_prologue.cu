@@ -68,11 +68,12 @@ __device__ double block_max(double v, double* sh) {
   return v;
 }
 
-// One CTA per object.
-template <typename YT>
+// One CTA per object.  GLS: weighted statistics with w = 1/dy^2 (dy NULL:
+// unit weights) for the generalized periodogram.
+template <typename YT, bool GLS>
 __global__ void stats_kernel(const double* __restrict__ t, const YT* __restrict__ y,
-                             const int64_t* __restrict__ offsets, int64_t total_nt, int center,
-                             int norm, ObjInfo* __restrict__ obj) {
+                             const YT* __restrict__ dy, const int64_t* __restrict__ offsets,
+                             int64_t total_nt, int center, int norm, ObjInfo* __restrict__ obj) {
   __shared__ double sh[32];
   const int64_t o = blockIdx.x;
   int64_t b = 0, e = total_nt;
@@ -86,28 +87,41 @@ __global__ void stats_kernel(const double* __restrict__ t, const YT* __restrict_
     }
   }
   const int64_t n = e - b;
-  double sy = 0.0, tmin = INFINITY, tmax = -INFINITY, bad = 0.0;
+  double sy = 0.0, sw = 0.0, tmin = INFINITY, tmax = -INFINITY, bad = 0.0;
   for (int64_t j = b + threadIdx.x; j < e; j += blockDim.x) {
     double tj = t[j], yj = (double)y[j];
+    double wj = 1.0;
+    if (GLS && dy) {
+      const double ej = (double)dy[j];
+      if (!isfinite(ej) || !(ej > 0.0)) bad = 1.0;
+      wj = 1.0 / (ej * ej);
+    }
     if (!isfinite(tj) || !isfinite(yj)) bad = 1.0;
-    sy += yj;
+    sy += wj * yj;
+    sw += wj;
     tmin = fmin(tmin, tj);
     tmax = fmax(tmax, tj);
   }
   sy = block_sum(sy, sh);
+  sw = block_sum(sw, sh);
   tmin = block_min(tmin, sh);
   tmax = block_max(tmax, sh);
   bad = block_sum(bad, sh);
-  const double mean = (center && n > 0) ? sy / (double)n : 0.0;
+  const double mean = ((GLS || center) && n > 0 && sw > 0.0) ? sy / sw : 0.0;
   double s2 = 0.0;
   for (int64_t j = b + threadIdx.x; j < e; j += blockDim.x) {
     double d = (double)y[j] - mean;
-    s2 += d * d;
+    double wj = 1.0;
+    if (GLS && dy) {
+      const double ej = (double)dy[j];
+      wj = 1.0 / (ej * ej);
+    }
+    s2 += wj * d * d;
   }
   s2 = block_sum(s2, sh);
   if (threadIdx.x == 0) {
     if (bad > 0.0) flags |= LSP_FLAG_NONFINITE;
-    if (n < 2) flags |= LSP_FLAG_FEW_OBS;
+    if (n < (GLS ? 3 : 2)) flags |= LSP_FLAG_FEW_OBS;
     if (!(flags & LSP_FLAG_NONFINITE) && n > 0 && !(s2 > 0.0)) flags |= LSP_FLAG_ZERO_VAR;
     ObjInfo oi;
     oi.t0 = n > 0 ? 0.5 * (tmin + tmax) : 0.0;
@@ -116,9 +130,13 @@ __global__ void stats_kernel(const double* __restrict__ t, const YT* __restrict_
     oi.begin = b;
     oi.n = (int32_t)n;
     oi.flags = flags;
-    oi.norm_scale = (norm && s2 > 0.0) ? 2.0 / s2 : 1.0;
+    if (GLS)  // the generalized power is normalised in the kernel; PSD form = P * sum_y2 / 2
+      oi.norm_scale = norm ? 1.0 : 0.5 * s2;
+    else
+      oi.norm_scale = (norm && s2 > 0.0) ? 2.0 / s2 : 1.0;
     oi.norm_scale_f = (float)oi.norm_scale;
-    oi.pad[0] = oi.pad[1] = oi.pad[2] = 0;
+    oi.wsum = sw;
+    oi.wsum_f = (float)sw;
     obj[o] = oi;
   }
 }
@@ -135,10 +153,10 @@ __device__ __forceinline__ uint64_t frac_fixed64(double f, double x) {
 }
 
 // grid.x: object; grid.y: slices of a single large object's observations.
-template <typename YT, typename Rec>
+template <typename YT, typename Rec, bool GLS>
 __global__ void records_kernel(const double* __restrict__ t, const YT* __restrict__ y,
-                               const ObjInfo* __restrict__ obj, int64_t slice, double f_min,
-                               double df, Rec* __restrict__ rec) {
+                               const YT* __restrict__ dy, const ObjInfo* __restrict__ obj,
+                               int64_t slice, double f_min, double df, Rec* __restrict__ rec) {
   const ObjInfo oi = obj[blockIdx.x];
   if (oi.flags & (LSP_FLAG_BAD_OFFSETS | LSP_FLAG_NONFINITE)) return;
   const int64_t lo = oi.begin + (int64_t)blockIdx.y * slice;
@@ -150,7 +168,12 @@ __global__ void records_kernel(const double* __restrict__ t, const YT* __restric
     const uint64_t bb = frac_fixed64(df, tp);
     double s, c;
     sincospi(2.0 * ((double)(int64_t)bb * 5.421010862427522e-20), &s, &c);  // 2^-64
-    const double yc = (double)y[j] - oi.ymean;
+    double w = 1.0;
+    if (GLS && dy) {
+      const double ej = (double)dy[j];
+      w = 1.0 / (ej * ej);
+    }
+    const double yc = (GLS ? w : 1.0) * ((double)y[j] - oi.ymean);
     Rec r;
     if constexpr (sizeof(Rec) == sizeof(RecF32)) {
       r.y = (float)yc;
@@ -160,14 +183,14 @@ __global__ void records_kernel(const double* __restrict__ t, const YT* __restric
       r.a_lo = (uint32_t)a;
       r.b_hi = (uint32_t)(bb >> 32);
       r.b_lo = (uint32_t)bb;
-      r.pad = 0;
+      r.pad = GLS ? __float_as_uint((float)w) : 0u;
     } else {
       r.y = yc;
       r.cr = c;
       r.sr = s;
       r.a = a;
       r.b = bb;
-      r.pad = 0;
+      r.pad = GLS ? (uint64_t)__double_as_longlong(w) : 0ull;
     }
     rec[j] = r;
   }
@@ -222,21 +245,31 @@ __global__ void scatter_kernel(const ObjInfo* __restrict__ obj, int64_t n_obj, u
 
 cudaError_t launch_stats(const double* t, const void* y, bool y64, const int64_t* offsets,
                          int64_t n_obj, int64_t total_nt, int center, int norm, ObjInfo* obj,
-                         cudaStream_t stream) {
+                         cudaStream_t stream, bool gls, const void* dy) {
   if (n_obj <= 0) return cudaSuccess;
   const int threads = n_obj == 1 ? 1024 : 128;
-  if (y64)
-    stats_kernel<double><<<(unsigned)n_obj, threads, 0, stream>>>(
-        t, (const double*)y, offsets, total_nt, center, norm, obj);
-  else
-    stats_kernel<float><<<(unsigned)n_obj, threads, 0, stream>>>(
-        t, (const float*)y, offsets, total_nt, center, norm, obj);
+  const unsigned g = (unsigned)n_obj;
+  if (y64) {
+    if (gls)
+      stats_kernel<double, true><<<g, threads, 0, stream>>>(t, (const double*)y, (const double*)dy, offsets,
+                                                             total_nt, center, norm, obj);
+    else
+      stats_kernel<double, false><<<g, threads, 0, stream>>>(t, (const double*)y, nullptr, offsets,
+                                                              total_nt, center, norm, obj);
+  } else {
+    if (gls)
+      stats_kernel<float, true><<<g, threads, 0, stream>>>(t, (const float*)y, (const float*)dy, offsets,
+                                                            total_nt, center, norm, obj);
+    else
+      stats_kernel<float, false><<<g, threads, 0, stream>>>(t, (const float*)y, nullptr, offsets, total_nt,
+                                                             center, norm, obj);
+  }
   return cudaGetLastError();
 }
 
 cudaError_t launch_records(const double* t, const void* y, bool y64, const ObjInfo* obj,
                            int64_t n_obj, int64_t max_nt_single, double f_min, double df,
-                           bool rec64, void* rec, cudaStream_t stream) {
+                           bool rec64, void* rec, cudaStream_t stream, bool gls, const void* dy) {
   if (n_obj <= 0) return cudaSuccess;
   int64_t slice = INT64_MAX / 4;
   unsigned gy = 1;
@@ -248,21 +281,23 @@ cudaError_t launch_records(const double* t, const void* y, bool y64, const ObjIn
     threads = 256;
   }
   dim3 grid((unsigned)n_obj, gy);
+#define LSP_REC(YT, REC, G)                                                                        \
+  records_kernel<YT, REC, G><<<grid, threads, 0, stream>>>(t, (const YT*)y, (const YT*)dy, obj, slice, \
+                                                            f_min, df, (REC*)rec)
   if (rec64) {
-    if (y64)
-      records_kernel<double, RecF64><<<grid, threads, 0, stream>>>(t, (const double*)y, obj, slice,
-                                                                   f_min, df, (RecF64*)rec);
-    else
-      records_kernel<float, RecF64><<<grid, threads, 0, stream>>>(t, (const float*)y, obj, slice,
-                                                                  f_min, df, (RecF64*)rec);
+    if (y64) {
+      if (gls) LSP_REC(double, RecF64, true); else LSP_REC(double, RecF64, false);
+    } else {
+      if (gls) LSP_REC(float, RecF64, true); else LSP_REC(float, RecF64, false);
+    }
   } else {
-    if (y64)
-      records_kernel<double, RecF32><<<grid, threads, 0, stream>>>(t, (const double*)y, obj, slice,
-                                                                   f_min, df, (RecF32*)rec);
-    else
-      records_kernel<float, RecF32><<<grid, threads, 0, stream>>>(t, (const float*)y, obj, slice,
-                                                                  f_min, df, (RecF32*)rec);
+    if (y64) {
+      if (gls) LSP_REC(double, RecF32, true); else LSP_REC(double, RecF32, false);
+    } else {
+      if (gls) LSP_REC(float, RecF32, true); else LSP_REC(float, RecF32, false);
+    }
   }
+#undef LSP_REC
   return cudaGetLastError();
 }
 

@@ -1,0 +1,124 @@
+"""GPU parity of the generalized periodogram (Section 4.11) against the
+oracle's weighted three-parameter least squares.
+
+Tolerances as for the standard path: FP32 <= 1e-4 absolute in the
+normalised power, FP64 <= 1e-10; argmax within one bin (FP32, tie-aware)
+or exact (FP64).
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+TOL = {"fp32": 1e-4, "fp64": 1e-10}
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("GPU tests need CUDA")
+    from paper_2105_04006_gb300 import build
+    build.build()
+    oracle.build()
+    import paper_2105_04006_gb300 as lsp
+    return lsp, torch, torch.device("cuda", 0)
+
+
+def _batch(seed=31, n_obj=30, n_f=5003):
+    b = synth.ragged_survey(n_obj, seed=seed, grid=synth.Grid(0.24, 12.0, n_f))
+    g = np.random.default_rng(seed)
+    dy = g.uniform(0.02, 0.3, b.t.size)
+    return b, dy
+
+
+def _run(env, b, dy, precision, **kw):
+    lsp, torch, dev = env
+    dt = torch.float32 if precision == "fp32" else torch.float64
+    t = torch.tensor(b.t, dtype=torch.float64, device=dev)
+    y = torch.tensor(b.y, dtype=dt, device=dev)
+    e = None if dy is None else torch.tensor(dy, dtype=dt, device=dev)
+    off = torch.tensor(b.offsets, dtype=torch.int64, device=dev)
+    g = lsp.Grid(b.grid.f_min, b.grid.f_max, b.grid.n_f)
+    p, pk = lsp.batch_gls(t, y, e, off, g, return_power=True, precision=precision, **kw)
+    torch.cuda.synchronize()
+    return p.cpu().numpy().astype(np.float64), lsp.peaks_to_numpy(pk)
+
+
+def _seen(a, precision):
+    return None if a is None else (a.astype(np.float32).astype(np.float64) if precision == "fp32" else a)
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+@pytest.mark.parametrize("weighted", [True, False])
+def test_gls_batch_matches_oracle(env, precision, weighted):
+    b, dy = _batch()
+    dy = dy if weighted else None
+    p, pk = _run(env, b, dy, precision)
+    ref = oracle.gls_batch(b.t, _seen(b.y, precision), _seen(dy, precision), b.offsets, b.grid.f_min,
+                           b.grid.f_max, b.grid.n_f)
+    err = np.max(np.abs(p - ref["power"]))
+    assert err <= TOL[precision], err
+    for o in range(b.n_obj):
+        if precision == "fp64":
+            assert pk["idx"][o] == ref["arg_idx"][o]
+        elif abs(int(pk["idx"][o]) - int(ref["arg_idx"][o])) > 1:
+            assert ref["power"][o][pk["idx"][o]] >= ref["arg_pow"][o] - TOL["fp32"]
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_gls_psd_form_and_k8(env, precision):
+    b, dy = _batch(seed=32, n_obj=12)
+    p, _ = _run(env, b, dy, precision, norm="psd", k_reseed=8)
+    ref = oracle.gls_batch(b.t, _seen(b.y, precision), _seen(dy, precision), b.offsets, b.grid.f_min,
+                           b.grid.f_max, b.grid.n_f, norm=0)["power"]
+    assert np.max(np.abs(p - ref)) <= TOL[precision] * max(1.0, np.abs(ref).max())
+
+
+def test_gls_single_object_entry_point(env):
+    lsp, torch, dev = env
+    b = synth.single_small(n_t=700, grid=synth.Grid(0.1, 10.0, 9001))
+    dy = np.random.default_rng(4).uniform(0.05, 0.2, b.t.size)
+    t = torch.tensor(b.t, dtype=torch.float64, device=dev)
+    y = torch.tensor(b.y.astype(np.float32), device=dev)
+    e = torch.tensor(dy.astype(np.float32), device=dev)
+    g = lsp.Grid(b.grid.f_min, b.grid.f_max, b.grid.n_f)
+    opts = lsp.make_opts()
+    ws = torch.empty(lsp.workspace_size_gls(1, b.t.size, g, opts), dtype=torch.uint8, device=dev)
+    power = torch.empty(g.n_f, dtype=torch.float32, device=dev)
+    peaks = torch.empty(40, dtype=torch.uint8, device=dev)
+    st = lsp.lib().lsp_periodogram_gls(ctypes.c_void_p(t.data_ptr()), ctypes.c_void_p(y.data_ptr()),
+                                       ctypes.c_void_p(e.data_ptr()), b.t.size, ctypes.byref(g), ctypes.byref(opts),
+                                       ctypes.c_void_p(power.data_ptr()), ctypes.c_void_p(peaks.data_ptr()),
+                                       ctypes.c_void_p(ws.data_ptr()), ws.numel(), None)
+    assert st == 0
+    torch.cuda.synchronize()
+    ref = oracle.gls_batch(b.t, _seen(b.y, "fp32"), _seen(dy, "fp32"), b.offsets, g.f_min, g.f_max, g.n_f)
+    assert np.max(np.abs(power.cpu().numpy() - ref["power"][0])) <= 1e-4
+    assert abs(int(lsp.peaks_to_numpy(peaks)["idx"][0]) - int(ref["arg_idx"][0])) <= 1
+
+
+def test_gls_degenerate_objects_and_nightly_cadence(env):
+    rng = np.random.default_rng(9)
+    segs = [(np.array([60000.0, 60001.0]), np.array([1.0, 2.0]), np.array([0.1, 0.1])),   # two obs
+            (np.array([60000.0, 60001.0, 60003.0]), np.array([1.0, 1.0, 1.0]), np.array([0.1, 0.2, 0.1])),
+            (np.array([60000.0, 60001.0, 60003.0]), np.array([1.0, 2.0, 1.0]), np.array([0.1, 0.0, 0.1]))]
+    for _ in range(6):  # one-hour nightly windows: ill-conditioned daily aliases
+        n = int(rng.integers(30, 300))
+        nights = np.sort(rng.choice(3000, n, replace=False)).astype(np.float64)
+        t = 60000.0 + nights + 0.3 + rng.uniform(0, 1 / 24, n)
+        y = 0.4 * np.sin(2 * np.pi * rng.uniform(0.3, 5.0) * t) + rng.normal(0, 0.2, n) + 3.0
+        segs.append((t, y, rng.uniform(0.05, 0.3, n)))
+    t = np.concatenate([s[0] for s in segs])
+    y = np.concatenate([s[1] for s in segs])
+    dy = np.concatenate([s[2] for s in segs])
+    off = np.concatenate([[0], np.cumsum([len(s[0]) for s in segs])]).astype(np.int64)
+    b = synth.Batch(t, y, off, synth.Grid(0.24, 12.0, 20011), np.zeros(len(segs)), np.zeros(len(segs)))
+    p, pk = _run(env, b, dy, "fp32")
+    ref = oracle.gls_batch(b.t, _seen(b.y, "fp32"), _seen(dy, "fp32"), b.offsets, 0.24, 12.0, 20011)
+    np.testing.assert_array_equal(pk["flags"], ref["flags"])
+    assert np.max(np.abs(p - ref["power"])) <= 1e-4
