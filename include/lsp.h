@@ -18,6 +18,11 @@
  *     the caller; the library never frees them and never keeps them past
  *     the call (plans keep nothing either, except what lsp_plan_execute
  *     captured into a CUDA graph, see there).
+ *   - An output array (power_out, peaks) may also be page-locked host memory
+ *     that the GPU can address (cudaHostAlloc, cudaHostRegister, or a pinned
+ *     torch tensor): the kernels then write the periodogram straight to the
+ *     host while they compute -- the library's form of the paper's
+ *     periodogram return (Section 3.5), without staging buffers.
  *   - Every compute entry point is asynchronous on `stream` (0 = the legacy
  *     default stream) and performs no device allocation: scratch memory is
  *     the caller's `workspace` (size from lsp_workspace_size) or a plan's.
@@ -243,8 +248,10 @@ lsp_status lsp_plan_execute(lsp_plan* plan, const double* t, const void* y, cons
 
 /*
  * End-to-end variant on HOST buffers: copies t, y, offsets to the device,
- * runs the plan, copies the peaks (and the periodogram when power_out is
- * not NULL) back, and synchronises `stream` before returning.  Pinned host
+ * runs the plan, copies the peaks back, and synchronises `stream` before
+ * returning.  The periodogram (when power_out is not NULL) is written by the
+ * kernels directly into power_out if it is page-locked host memory, and
+ * otherwise computed into a device buffer and copied back.  Pinned host
  * memory gives the fastest copies.  The first call allocates the plan's
  * device staging buffers (later calls reuse them).
  */

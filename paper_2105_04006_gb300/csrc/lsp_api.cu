@@ -704,7 +704,17 @@ lsp_status lsp_plan_execute_host(lsp_plan* p, const double* t, const void* y,
   if ((st = alloc(&p->d_y, p->total_nt * ysz))) return st;
   if ((st = alloc((void**)&p->d_off, (p->n_obj + 1) * sizeof(int64_t)))) return st;
   if ((st = alloc((void**)&p->d_peaks, n_peaks * sizeof(lsp_peak)))) return st;
-  if (power_out && (st = alloc(&p->d_power, pbytes))) return st;
+  // A page-locked, device-addressable power_out is written by the kernels
+  // directly (zero copy over the chip-to-chip link); otherwise stage it.
+  void* power_direct = nullptr;
+  if (power_out) {
+    cudaPointerAttributes attr;
+    if (cudaPointerGetAttributes(&attr, power_out) == cudaSuccess && attr.type == cudaMemoryTypeHost &&
+        attr.devicePointer)
+      power_direct = attr.devicePointer;
+    cudaGetLastError();
+  }
+  if (power_out && !power_direct && (st = alloc(&p->d_power, pbytes))) return st;
   LSP_CUDA(cudaMemcpyAsync(p->d_t, t, p->total_nt * sizeof(double), cudaMemcpyHostToDevice, s), "H2D t");
   LSP_CUDA(cudaMemcpyAsync(p->d_y, y, p->total_nt * ysz, cudaMemcpyHostToDevice, s), "H2D y");
   const int64_t* d_off = nullptr;
@@ -713,13 +723,14 @@ lsp_status lsp_plan_execute_host(lsp_plan* p, const double* t, const void* y,
                              cudaMemcpyHostToDevice, s), "H2D offsets");
     d_off = p->d_off;
   }
-  st = lsp_plan_execute(p, p->d_t, p->d_y, d_off, power_out ? p->d_power : nullptr,
+  st = lsp_plan_execute(p, p->d_t, p->d_y, d_off,
+                        power_direct ? power_direct : (power_out ? p->d_power : nullptr),
                         peaks ? p->d_peaks : nullptr, stream);
   if (st) return st;
   if (peaks)
     LSP_CUDA(cudaMemcpyAsync(peaks, p->d_peaks, n_peaks * sizeof(lsp_peak), cudaMemcpyDeviceToHost, s),
              "D2H peaks");
-  if (power_out)
+  if (power_out && !power_direct)
     LSP_CUDA(cudaMemcpyAsync(power_out, p->d_power, pbytes, cudaMemcpyDeviceToHost, s), "D2H power");
   LSP_CUDA(cudaStreamSynchronize(s), "synchronize");
   return LSP_OK;

@@ -433,3 +433,39 @@ def test_full_ragged_lognormal_top3_sampled(env):
             if abs(kg - ko) > 1:
                 assert abs(pr[kg] - pr[ko]) <= 2 * TOL32, (o, r, kg, ko)
             assert abs(pk["power"][o, r] - ref["top_pow"][i, r]) <= 2 * TOL32
+
+
+def test_periodogram_written_to_pinned_host_memory(env, small_batch):
+    """power_out in page-locked host memory: the kernels write it directly (Section 3.5's return)."""
+    lsp, torch, dev = env
+    b, ref = small_batch
+    g = lsp.Grid(b.grid.f_min, b.grid.f_max, b.grid.n_f)
+    t = _dev(torch, dev, b.t, torch.float64)
+    y = _dev(torch, dev, b.y, torch.float32)
+    off = _dev(torch, dev, b.offsets, torch.int64)
+    p_dev, pk_dev = lsp.batch(t, y, off, g, return_power=True)
+    host = torch.empty((b.n_obj, g.n_f), dtype=torch.float32).pin_memory()
+    host.fill_(-1.0)
+    opts = lsp.make_opts()
+    ws = torch.empty(lsp.workspace_size(b.n_obj, b.t.size, g, opts), dtype=torch.uint8, device=dev)
+    peaks = torch.empty(b.n_obj * 40, dtype=torch.uint8, device=dev)
+    import ctypes
+    st = lsp.lib().lsp_batch(ctypes.c_void_p(t.data_ptr()), ctypes.c_void_p(y.data_ptr()),
+                             ctypes.c_void_p(off.data_ptr()), b.n_obj, b.t.size, ctypes.byref(g), ctypes.byref(opts),
+                             ctypes.c_void_p(host.data_ptr()), ctypes.c_void_p(peaks.data_ptr()),
+                             ctypes.c_void_p(ws.data_ptr()), ws.numel(),
+                             ctypes.c_void_p(torch.cuda.current_stream(dev).cuda_stream))
+    assert st == 0
+    torch.cuda.synchronize()
+    assert torch.equal(host, p_dev.cpu())
+    # the host entry point takes the same zero-copy route for a pinned power_out
+    plan = lsp.Plan(b.n_obj, b.t.size, g)
+    host2 = torch.full((b.n_obj, g.n_f), -1.0, dtype=torch.float32).pin_memory()
+    pk = plan.execute_host(b.t, b.y.astype(np.float32), b.offsets, power=host2)
+    assert torch.equal(host2, p_dev.cpu())
+    assert (pk["idx"] == lsp.peaks_to_numpy(pk_dev)["idx"]).all()
+    # and the staged route for pageable memory
+    host3 = np.full((b.n_obj, g.n_f), -1.0, dtype=np.float32)
+    plan.execute_host(b.t, b.y.astype(np.float32), b.offsets, power=host3)
+    np.testing.assert_array_equal(host3, p_dev.cpu().numpy())
+    plan.close()
