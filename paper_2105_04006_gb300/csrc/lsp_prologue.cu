@@ -166,8 +166,23 @@ __global__ void records_kernel(const double* __restrict__ t, const YT* __restric
     const double tp = t[j] - oi.t0;
     const uint64_t a = frac_fixed64(f_min, tp);
     const uint64_t bb = frac_fixed64(df, tp);
+    const double xb = (double)(int64_t)bb * 5.421010862427522e-20;  // 2^-64: cycles in [-1/2, 1/2)
     double s, c;
-    sincospi(2.0 * ((double)(int64_t)bb * 5.421010862427522e-20), &s, &c);  // 2^-64
+    if constexpr (sizeof(Rec) == sizeof(RecF32)) {
+      // FP32 rotation: sincospi of the fraction's leading float, corrected to
+      // first order for the remainder (|lo| < 2^-25 cycle): accurate to about
+      // one FP32 ulp without an FP64 transcendental (GB300's FP64 pipe is
+      // 1/64 of its FP32 rate).
+      const float hi = (float)xb;
+      const float lo = (float)(xb - (double)hi);
+      float sh, ch;
+      sincospif(2.0f * hi, &sh, &ch);
+      const float d = 6.28318530717958647692f * lo;
+      c = (double)fmaf(-sh, d, ch);
+      s = (double)fmaf(ch, d, sh);
+    } else {
+      sincospi(2.0 * xb, &s, &c);
+    }
     double w = 1.0;
     if (GLS && dy) {
       const double ej = (double)dy[j];
@@ -274,11 +289,11 @@ cudaError_t launch_records(const double* t, const void* y, bool y64, const ObjIn
   int64_t slice = INT64_MAX / 4;
   unsigned gy = 1;
   int threads = 128;
-  if (n_obj == 1) {  // spread one large object over many CTAs
-    slice = 4096;
+  if (n_obj == 1) {  // spread one object over many CTAs (FP64 work is slow per SM)
+    slice = 256;
     gy = (unsigned)((max_nt_single + slice - 1) / slice);
     if (gy == 0) gy = 1;
-    threads = 256;
+    threads = 128;
   }
   dim3 grid((unsigned)n_obj, gy);
 #define LSP_REC(YT, REC, G)                                                                        \
