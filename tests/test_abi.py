@@ -143,3 +143,36 @@ def test_grid_rule_reproduces_table2(lsp_mod):
         assert g.n_f == n_f, (name, g.n_f, n_f)
     with pytest.raises(lsp_mod.LSPError):
         lsp_mod.grid_for_span(1.0, 2.0, 0.0)
+
+
+def test_newer_entry_points_validate_without_launch(lsp_mod):
+    L = lsp_mod.lib()
+    g = lsp_mod.Grid(0.24, 12.0, 1000)
+    o = lsp_mod.make_opts()
+    P = ctypes.c_void_p
+    # generalized periodogram: workspace query, NULL offsets, too-small workspace
+    n = ctypes.c_size_t()
+    assert L.lsp_workspace_size_gls(10, 1000, ctypes.byref(g), ctypes.byref(o), ctypes.byref(n)) == 0
+    assert n.value >= lsp_mod.workspace_size(10, 1000, g, o) // 2 and n.value % 256 == 0
+    assert L.lsp_batch_gls(P(256), P(512), None, None, 10, 1000, ctypes.byref(g), ctypes.byref(o), None, None,
+                           None, 0, None) == 1
+    assert L.lsp_batch_gls(P(256), P(512), None, P(768), 10, 1000, ctypes.byref(g), ctypes.byref(o), None, None,
+                           P(1024), 16, None) == 4
+    # learned stage: parameter count and argument checks
+    dims = lsp_mod.MlpDims(512, 256, 3, 98)
+    cnt = ctypes.c_int64()
+    assert L.lsp_mlp_param_count(ctypes.byref(dims), ctypes.byref(cnt)) == 0
+    assert cnt.value == 512 * 256 + 256 + 2 * (256 * 256 + 256) + 256 * 98 + 98
+    bad = lsp_mod.MlpDims(512, 256, 0, 98)
+    assert L.lsp_mlp_param_count(ctypes.byref(bad), ctypes.byref(cnt)) == 1
+    assert L.lsp_top_classes(P(256), 4, 10, 17, P(512), None) == 1  # k > 16
+    assert L.lsp_featurize(P(256), P(512), P(768), 3, 100, ctypes.byref(g), ctypes.c_float(0.0), P(1024), None,
+                           None) == 1  # lag_max must be > 0
+    assert L.lsp_refine_windows(P(256), P(512), P(768), 3, 100, ctypes.byref(g), 1, P(1024), 8, 4096, 1024,
+                                ctypes.c_float(0.5), ctypes.c_float(0.3), 1, P(2048), None, P(4096), 1 << 20,
+                                None) == 1  # window > 2048
+    assert L.lsp_refine_windows(P(256), P(512), P(768), 3, 100, ctypes.byref(g), 1, P(1024), 8, 2048, 1024,
+                                ctypes.c_float(0.5), ctypes.c_float(0.3), 1, P(2048), None, P(4096), 16,
+                                None) == 1  # workspace too small
+    # grid rule
+    assert lsp_mod.grid_for_span(0.24, 12.0, 3650.0).n_f == round((12.0 - 0.24) / (0.1 / 3650.0))
