@@ -38,7 +38,8 @@ sys.path.insert(0, ROOT)
 import synth  # noqa: E402
 
 METRIC = "objects/sec and trig-sum evals/s (N_t*N_f) vs FP32 roofline; learned vs plain"
-FP32_OPS_PER_PAIR = 8      # 2 FMUL + 2 FFMA (rotation) + 4 FFMA (XC, XS, CC, CS)
+OPS_PER_PAIR = 6           # 2 FFMA (three-term recurrence step) + 4 FFMA (XC, XS, CC, CS); a chain of K
+                           # pairs spends 4 on its one rotation and 2 (K - 2) on three-term steps: 6K in all
 FP32_LANES_PER_SM = 128    # FP32 lanes per SM per clock
 FP64_LANES_PER_SM = 2      # FP64 FMAs per SM per clock: 1.25 TFLOP/s nominal / (2 x 152 SMs x 2.07 GHz)
 
@@ -330,8 +331,8 @@ def run_gpu(args, w, name):
     achieved = pairs / (main_avg / 1e3) / 1e9
     clk_mhz = (clocks or {}).get("sm_mhz") or 0.0
     lanes = FP64_LANES_PER_SM if fp64 else FP32_LANES_PER_SM
-    peak = n_sm * lanes * clk_mhz * 1e6 / FP32_OPS_PER_PAIR / 1e9 if clk_mhz else None
-    peak_max = n_sm * lanes * 2070e6 / FP32_OPS_PER_PAIR / 1e9
+    peak = n_sm * lanes * clk_mhz * 1e6 / OPS_PER_PAIR / 1e9 if clk_mhz else None
+    peak_max = n_sm * lanes * 2070e6 / OPS_PER_PAIR / 1e9
     src = source_hash()
     traffic = recorded_traffic(name, src)
 
@@ -352,7 +353,7 @@ def run_gpu(args, w, name):
                          "frac": (achieved / peak) if peak else None, "traffic": traffic,
                          "kernel": "main trig-sum kernel", "main_kernel_ms": main_avg,
                          "peak_basis": f"{n_sm} SMs x {lanes} {'FP64' if fp64 else 'FP32'} lanes x sampled SM "
-                                       f"clock / {FP32_OPS_PER_PAIR} ops per pair",
+                                       f"clock / {OPS_PER_PAIR} ops per pair",
                          "peak_at_max_clock": peak_max, "source_hash": src},
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": "objects/s", "h2d_bytes_per_step": int(h2d),

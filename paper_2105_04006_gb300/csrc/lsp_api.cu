@@ -124,16 +124,16 @@ lsp_status resolve(int64_t n_obj, int64_t total_nt, const lsp_grid* g, const lsp
     packed = cfg->packed;
     split_req = cfg->obs_split;
   } else {
-    // generalized kernels keep six sums per frequency: shorter FP32 chains
-    k = o.k_reseed ? o.k_reseed : ((gls && l.prec == LSP_FP32) ? 4 : 8);
+    k = o.k_reseed ? o.k_reseed : 8;
     if (l.prec == LSP_FP64) {
       fpt = o.freqs_per_thread ? o.freqs_per_thread : k;
       threads = o.block_threads ? o.block_threads : 128;
     } else {
       fpt = o.freqs_per_thread ? o.freqs_per_thread
                                : (main_variant_exists(0, 1, k, 2 * k) ? 2 * k : k);
-      // measured on GB300: 128-thread CTAs for batches, 256 for one object
-      threads = o.block_threads ? o.block_threads : (n_obj > 1 ? 128 : 256);
+      // measured on GB300: 128-thread CTAs for batches and for the generalized
+      // kernels (six sums per frequency), 256 for one object
+      threads = o.block_threads ? o.block_threads : ((n_obj > 1 || gls) ? 128 : 256);
     }
     packed = (l.prec == LSP_FP32 && fpt == 2 * k) ? 1 : 0;
     split_req = o.obs_split;

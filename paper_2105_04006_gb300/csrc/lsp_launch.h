@@ -11,6 +11,17 @@ struct lsp_peak;
 
 namespace lsp {
 
+// Opts a kernel in to `dyn` bytes of dynamic shared memory where its static
+// and dynamic shared memory together pass the 48 KB available by default.
+template <typename Kern>
+inline cudaError_t allow_dyn_smem(Kern kern, size_t dyn) {
+  cudaFuncAttributes a{};
+  cudaError_t e = cudaFuncGetAttributes(&a, kern);
+  if (e != cudaSuccess) return e;
+  if (dyn + a.sharedSizeBytes <= 48 * 1024) return cudaSuccess;
+  return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+}
+
 // Prologue, Section 2 (zero-mean magnitudes) and the per-observation phase
 // data of the rotation recurrence.  y is float (y64 = false) or double.
 // gls: weighted statistics / records of the generalized periodogram (dy

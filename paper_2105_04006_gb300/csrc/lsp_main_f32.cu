@@ -8,10 +8,8 @@ namespace {
 template <typename Kern, typename P>
 cudaError_t launch_kernel(Kern kern, const MainLaunch& ml, const P& p, cudaStream_t stream) {
   size_t dyn = main_dyn_smem(ml.prec, ml.fpt, ml.threads, ml.top);
-  if (dyn > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
-    if (e != cudaSuccess) return e;
-  }
+  cudaError_t e = allow_dyn_smem(kern, dyn);
+  if (e != cudaSuccess) return e;
   kern<<<ml.grid, ml.threads, dyn, stream>>>(p);
   return cudaGetLastError();
 }
@@ -19,7 +17,7 @@ cudaError_t launch_kernel(Kern kern, const MainLaunch& ml, const P& p, cudaStrea
 template <typename Kern>
 int occupancy(Kern kern, int threads, size_t dyn) {
   int nb = 0;
-  if (dyn > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+  if (allow_dyn_smem(kern, dyn) != cudaSuccess) return 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, threads, dyn) != cudaSuccess) return 0;
   return nb;
 }

@@ -32,8 +32,8 @@ int main_blocks_per_sm_f64(int k, int fpt, int threads, int top, int gls) {
   int nb = 0;
   size_t dyn = main_dyn_smem(1, fpt, threads, top);
   dispatch_f64(k, gls, [&](auto kern) {
-    if (dyn > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, threads, dyn) != cudaSuccess) nb = 0;
+    if (allow_dyn_smem(kern, dyn) != cudaSuccess || cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, threads, dyn) != cudaSuccess)
+      nb = 0;
   });
   return nb;
 }
@@ -58,10 +58,8 @@ cudaError_t launch_main_f64(const MainLaunch& ml, cudaStream_t stream) {
   cudaError_t err = cudaErrorInvalidValue;
   size_t dyn = main_dyn_smem(1, ml.fpt, ml.threads, ml.top);
   dispatch_f64(ml.k_reseed, ml.gls, [&](auto kern) {
-    if (dyn > 48 * 1024) {
-      err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
-      if (err != cudaSuccess) return;
-    }
+    err = allow_dyn_smem(kern, dyn);
+    if (err != cudaSuccess) return;
     kern<<<ml.grid, ml.threads, dyn, stream>>>(p);
     err = cudaGetLastError();
   });

@@ -15,12 +15,13 @@
 //   - observations are staged through shared memory in tiles and read by
 //     all threads at once (broadcast), so every (t, y) load is shared by the
 //     CTA's blockDim.x * F frequencies;
-//   - sin/cos come from a rotation recurrence across the uniform grid,
-//     (c, s) <- (c cr - s sr, s cr + c sr) with (cr, sr) = e^{2 pi i df t'},
-//     reseeded from the exact fixed-point phase every K frequencies (the
-//     paper, Section 4.5, rejects the recurrence as serial; here it runs
-//     along a thread's own frequencies while threads, CTAs and objects run
-//     in parallel);
+//   - sin/cos come from a recurrence across the uniform grid, reseeded from
+//     the exact fixed-point phase every K frequencies (the paper, Section
+//     4.5, rejects the recurrence as serial; here it runs along a thread's
+//     own frequencies while threads, CTAs and objects run in parallel).
+//     One rotation by (cr, sr) = e^{2 pi i df t'} gives the second value,
+//     then a three-term recurrence of one FMA per component gives the rest
+//     (chain3 below): 6 FP32 operations per pair instead of the rotation's 8;
 //   - the FP32 kernel packs two reseed chains into f32x2 lanes, so one
 //     instruction advances two frequencies;
 //   - CTAs are persistent and pull (object, chunk, split) items from a queue
@@ -92,11 +93,12 @@ __device__ __forceinline__ Item decode_item(const P& p, int64_t item) {
 // lane 0 covers k0 .. k0+K-1, lane 1 covers k0+K .. k0+2K-1.
 //
 // The shared-memory tile holds the 32-byte records as they are.  Each
-// observation costs every thread two SFU seeds (one per chain) and 2K-1
-// packed recurrence steps.  (Measured alternatives that did not pay on
-// GB300: issuing the next observation's seeds one step ahead, integer
-// bit-building of the seed angle instead of I2F, and deriving the second
-// chain's seed from the first by a K-step rotation.)
+// observation costs every thread two SFU seeds (one per chain), one packed
+// rotation and K-2 packed three-term steps (chain3).  (Measured alternatives
+// that did not pay on GB300: issuing the next observation's seeds one step
+// ahead, integer bit-building of the seed angle instead of I2F, deriving the
+// second chain's seed from the first by a K-step rotation, unrolling the
+// observation loop by two, and unpacked scalar rotations.)
 
 __device__ __forceinline__ f2_t f2_of(uint32_t lo, uint32_t hi) {
   f2_t r;
@@ -104,39 +106,187 @@ __device__ __forceinline__ f2_t f2_of(uint32_t lo, uint32_t hi) {
   return r;
 }
 
-__device__ __forceinline__ void seed_pair(const uint4 w2, uint32_t k0, uint32_t k1, f2_t& c2, f2_t& s2) {
-  float c0, s0, c1, s1;
-  seed_sincos_f32(phase_hi32(w2.x, w2.y, w2.z, k0), c0, s0);
-  seed_sincos_f32(phase_hi32(w2.x, w2.y, w2.z, k1), c1, s1);
-  c2 = f2_pack(c0, c1);
-  s2 = f2_pack(s0, s1);
+// ------------------------------------------------------- three-term chains
+// Element-wise helpers for the three chain types: packed f32x2 pairs, float
+// and double.  neg_ flips the sign bit; dbl_ doubles by adding one to the
+// exponent field (exact for normal numbers; a zero or subnormal input, which
+// a rounded cos or sin of a grid step essentially never is, becomes a number
+// of magnitude <= 2^-125 instead, a negligible coefficient error).
+__device__ __forceinline__ f2_t mul_(f2_t a, f2_t b) { return f2_mul(a, b); }
+__device__ __forceinline__ f2_t fma_(f2_t a, f2_t b, f2_t c) { return f2_fma(a, b, c); }
+__device__ __forceinline__ f2_t neg_(f2_t a) { return a ^ 0x8000000080000000ull; }
+__device__ __forceinline__ f2_t dbl_(f2_t a) { return a + 0x0080000000800000ull; }
+__device__ __forceinline__ float mul_(float a, float b) { return a * b; }
+__device__ __forceinline__ float fma_(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ float neg_(float a) { return __uint_as_float(__float_as_uint(a) ^ 0x80000000u); }
+__device__ __forceinline__ float dbl_(float a) { return __uint_as_float(__float_as_uint(a) + 0x00800000u); }
+__device__ __forceinline__ double mul_(double a, double b) { return a * b; }
+__device__ __forceinline__ double fma_(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ double neg_(double a) {
+  return __longlong_as_double(__double_as_longlong(a) ^ (long long)0x8000000000000000ull);
+}
+__device__ __forceinline__ double dbl_(double a) {
+  return __longlong_as_double(__double_as_longlong(a) + (1ll << 52));
+}
+// |sin| > |cos| from the bit patterns (IEEE magnitudes order like integers).
+__device__ __forceinline__ bool sin_dominates(uint32_t cr_bits, uint32_t sr_bits) {
+  return (sr_bits & 0x7fffffffu) > (cr_bits & 0x7fffffffu);
+}
+__device__ __forceinline__ bool sin_dominates(double cr, double sr) {
+  return (__double_as_longlong(sr) & 0x7fffffffffffffffll) > (__double_as_longlong(cr) & 0x7fffffffffffffffll);
 }
 
-// K steps of the two packed reseed chains at one observation: accumulate the
-// four sums at the current (cos, sin), then rotate by one grid step.
-template <int K>
-__device__ __forceinline__ void recurrence_steps(f2_t (&xc)[K], f2_t (&xs)[K], f2_t (&cc)[K], f2_t (&cs)[K],
-                                                 f2_t c2, f2_t s2, f2_t y2, f2_t cr2, f2_t sr2, f2_t nsr2) {
+// One reseed chain at one observation: the K values e_m = e_0 e^{i m theta},
+// m = 0 .. K-1, theta = 2 pi df t', (cr, sr) = (cos theta, sin theta).
+// body(m, neg, c, s) receives (c, s) = sigma_m e_m, sigma_m = -1 when neg.
+//
+// e_1 = e_0 (cr + i sr) by one rotation (4 operations); the rest by one of
+// two three-term recurrences at 2 operations per step, chosen per
+// observation so that its error amplification stays <= sqrt 2:
+//   Chebyshev  e_{m+1} = 2 cos(theta) e_m - e_{m-1}   where |sin| > |cos|;
+//              a rounding error propagates as sin((n+1) theta) / sin theta
+//              and the coefficient's rounding moves theta by <= ulp cot(theta);
+//   leapfrog   e_{m+1} = e_{m-1} + 2 i sin(theta) e_m  elsewhere; its roots
+//              e^{i theta} and -e^{-i theta} stay 2 |cos theta| apart and
+//              the coefficient's rounding moves theta by <= ulp tan(theta).
+// The Chebyshev chain stores x_m = sigma_m e_m with sigma = + + - - + + ...,
+// which turns its subtraction into an FMA addend of + x_{m-1}:
+// x_{m+1} = (sigma_{m+1} sigma_m) 2 cr x_m + x_{m-1}, the product sign
+// alternating + - + - with m.  The choice is the same for every thread of a
+// CTA (one observation at a time), so the branch never diverges.
+template <int K, bool CHEB, typename T, typename Body>
+__device__ __forceinline__ void chain3_mode(T c, T s, T cr, T sr, T nsr, T coef, T ncoef, Body&& body) {
+  body(0, false, c, s);
+  if constexpr (K > 1) {
+    const T c1 = fma_(s, nsr, mul_(c, cr));
+    const T s1 = fma_(c, sr, mul_(s, cr));
+    body(1, false, c1, s1);
+    T cp = c, sp = s;
+    c = c1;
+    s = s1;
 #pragma unroll
-  for (int m = 0; m < K; ++m) {
-    xc[m] = f2_fma(y2, c2, xc[m]);
-    xs[m] = f2_fma(y2, s2, xs[m]);
-    cc[m] = f2_fma(c2, c2, cc[m]);
-    cs[m] = f2_fma(c2, s2, cs[m]);
-    if (m + 1 < K) {
-      const f2_t tc = f2_mul(c2, cr2);
-      const f2_t tsr = f2_mul(s2, cr2);
-      const f2_t cn = f2_fma(s2, nsr2, tc);
-      s2 = f2_fma(c2, sr2, tsr);
-      c2 = cn;
+    for (int m = 1; m + 1 < K; ++m) {
+      T cn, sn;
+      if constexpr (CHEB) {
+        const T cm = (m & 1) ? ncoef : coef;
+        cn = fma_(cm, c, cp);
+        sn = fma_(cm, s, sp);
+      } else {
+        cn = fma_(ncoef, s, cp);
+        sn = fma_(coef, c, sp);
+      }
+      cp = c;
+      sp = s;
+      c = cn;
+      s = sn;
+      body(m + 1, CHEB && ((m + 1) & 2) != 0, c, s);
     }
   }
+}
+
+// chain3_mode with the coefficients formed here and the form chosen at run
+// time: coef = 2 cr (Chebyshev, cheb true) or 2 sr (leapfrog).
+template <int K, typename T, typename Body>
+__device__ __forceinline__ void chain3(T c, T s, T cr, T sr, bool cheb, Body&& body) {
+  if (cheb) {
+    const T a = dbl_(cr);
+    chain3_mode<K, true>(c, s, cr, sr, neg_(sr), a, neg_(a), body);
+  } else {
+    const T b = dbl_(sr);
+    chain3_mode<K, false>(c, s, cr, sr, neg_(sr), b, neg_(b), body);
+  }
+}
+
+// ------------------------------------------------ expanded observation tile
+// The packed kernels stage each tile of observations into shared memory as
+// ObsF2 entries that hold every operand of the inner loop already paired for
+// f32x2 and already negated, with the tile's Chebyshev observations first
+// and its leapfrog observations after them (a stable partition by index,
+// so the summation order is fixed).  The inner loops then issue no packing,
+// sign or mode instructions and no per-observation branch.
+struct __align__(16) ObsF2 {
+  f2_t y, ny;         // {y, y}, {-y, -y}  (GLS: u = w (y - ybar_w))
+  f2_t cr, sr, nsr;   // cos, sin and -sin of the grid step angle theta
+  f2_t coef, ncoef;   // +-2 cos theta (Chebyshev) or +-2 sin theta (leapfrog)
+  uint32_t a_hi, b_hi, b_lo, kb_hi;  // phase words and the high word of K b
+};
+struct __align__(16) ObsF2W {
+  ObsF2 e;
+  f2_t w, nw;         // {w, w}, {-w, -w}, w = 1 / dy^2 (generalized periodogram)
+};
+
+__device__ __forceinline__ f2_t f2_dup(uint32_t v) { return f2_of(v, v); }
+
+__device__ __forceinline__ void expand_obs(const uint4 r0, const uint4 r1, bool cheb, uint32_t K, ObsF2& e) {
+  const uint32_t sign = 0x80000000u;
+  const uint32_t cf = cheb ? r0.y + 0x00800000u : r0.z + 0x00800000u;  // 2 cr or 2 sr (exponent + 1)
+  e.y = f2_dup(r0.x);
+  e.ny = f2_dup(r0.x ^ sign);
+  e.cr = f2_dup(r0.y);
+  e.sr = f2_dup(r0.z);
+  e.nsr = f2_dup(r0.z ^ sign);
+  e.coef = f2_dup(cf);
+  e.ncoef = f2_dup(cf ^ sign);
+  e.a_hi = r0.w;
+  e.b_hi = r1.x;
+  e.b_lo = r1.y;
+  e.kb_hi = K * r1.x + __umulhi(K, r1.y);  // high word of K b (mod 2^64)
+}
+__device__ __forceinline__ void expand_obs(const uint4 r0, const uint4 r1, bool cheb, uint32_t K, ObsF2W& e) {
+  expand_obs(r0, r1, cheb, K, e.e);
+  e.w = f2_dup(r1.w);
+  e.nw = f2_dup(r1.w ^ 0x80000000u);
+}
+
+// Stage records [0, nt) of src (32-byte RecF32, nt <= LSP_TILE_OBS) into
+// ent; returns the number of Chebyshev entries.  blockDim.x is a multiple of
+// 32, so each warp's 32 consecutive records form one ballot slice.
+template <typename Ent>
+__device__ __forceinline__ int stage_tile(const uint4* __restrict__ src, int nt, uint32_t K, Ent* ent,
+                                          uint32_t* s_bal) {
+  const int tid = threadIdx.x, lane = tid & 31;
+  for (int i = tid; i < LSP_TILE_OBS; i += blockDim.x) {
+    bool cheb = false;
+    if (i < nt) {
+      const uint4 r0 = __ldg(src + 2 * i);
+      cheb = sin_dominates(r0.y, r0.z);
+    }
+    const uint32_t bal = __ballot_sync(0xffffffffu, cheb);
+    if (lane == 0) s_bal[i >> 5] = bal;
+  }
+  __syncthreads();
+  int n_cheb = 0;
+#pragma unroll
+  for (int q = 0; q < LSP_TILE_OBS / 32; ++q) n_cheb += __popc(s_bal[q]);
+  for (int i = tid; i < nt; i += blockDim.x) {
+    const uint4 r0 = __ldg(src + 2 * i), r1 = __ldg(src + 2 * i + 1);
+    const int sl = i >> 5;
+    int before = 0;
+    for (int q = 0; q < sl; ++q) before += __popc(s_bal[q]);
+    const uint32_t b = s_bal[sl];
+    before += __popc(b & ((1u << lane) - 1u));
+    const bool cheb = (b >> lane) & 1u;
+    expand_obs(r0, r1, cheb, K, ent[cheb ? before : n_cheb + (i - before)]);
+  }
+  __syncthreads();
+  return n_cheb;
+}
+
+// Seeds of the two packed chains: bins k0 and k0 + K.
+__device__ __forceinline__ void seed_pair_kb(const ObsF2& e, uint32_t k0, f2_t& c2, f2_t& s2) {
+  float c0, s0, c1, s1;
+  const uint32_t ph0 = phase_hi32(e.a_hi, e.b_hi, e.b_lo, k0);
+  seed_sincos_f32(ph0, c0, s0);
+  seed_sincos_f32(ph0 + e.kb_hi, c1, s1);  // error <= 2^-31 cycle from the dropped carries
+  c2 = f2_pack(c0, c1);
+  s2 = f2_pack(s0, s1);
 }
 
 template <int K>
 __global__ void __launch_bounds__(256) main_f32_packed(MainParams<RecF32, float> p) {
   constexpr int F = 2 * K;
-  __shared__ uint4 s_obs[2 * LSP_TILE_OBS];
+  __shared__ ObsF2 s_ent[LSP_TILE_OBS];
+  __shared__ uint32_t s_bal[LSP_TILE_OBS / 32];
   __shared__ unsigned long long red[32];
   __shared__ uint32_t s_item;
   extern __shared__ __align__(16) unsigned char dyn_smem[];
@@ -172,18 +322,22 @@ __global__ void __launch_bounds__(256) main_f32_packed(MainParams<RecF32, float>
 
     for (int64_t ts = ob; ts < oe; ts += LSP_TILE_OBS) {
       const int nt = (int)((oe - ts) < LSP_TILE_OBS ? (oe - ts) : LSP_TILE_OBS);
-      const uint4* src = reinterpret_cast<const uint4*>(p.rec + ts);
-      for (int i = tid; i < 2 * nt; i += blockDim.x) s_obs[i] = __ldg(src + i);
-      __syncthreads();
-      for (int j = 0; j < nt; ++j) {
-        const uint4 r0 = s_obs[2 * j];
-        const uint4 r1 = s_obs[2 * j + 1];
+      const int n_ch = stage_tile(reinterpret_cast<const uint4*>(p.rec + ts), nt, (uint32_t)K, s_ent, s_bal);
+      auto obs = [&](const ObsF2& e, auto cheb_tag) {
         f2_t c2, s2;
-        seed_pair(make_uint4(r0.w, r1.x, r1.y, 0u), k0, k1, c2, s2);
-        const uint32_t nsr = r0.z ^ 0x80000000u;
-        recurrence_steps<K>(xc, xs, cc, cs, c2, s2, f2_of(r0.x, r0.x), f2_of(r0.y, r0.y),
-                            f2_of(r0.z, r0.z), f2_of(nsr, nsr));
-      }
+        seed_pair_kb(e, k0, c2, s2);
+        const f2_t y2 = e.y, ny2 = e.ny;
+        chain3_mode<K, decltype(cheb_tag)::value>(c2, s2, e.cr, e.sr, e.nsr, e.coef, e.ncoef,
+                                                  [&](int m, bool neg, f2_t c, f2_t s) {
+                                                    const f2_t yy = neg ? ny2 : y2;
+                                                    xc[m] = f2_fma(yy, c, xc[m]);
+                                                    xs[m] = f2_fma(yy, s, xs[m]);
+                                                    cc[m] = f2_fma(c, c, cc[m]);
+                                                    cs[m] = f2_fma(c, s, cs[m]);
+                                                  });
+      };
+      for (int j = 0; j < n_ch; ++j) obs(s_ent[j], std::true_type{});
+      for (int j = n_ch; j < nt; ++j) obs(s_ent[j], std::false_type{});
       __syncthreads();
     }
 
@@ -233,7 +387,8 @@ __global__ void __launch_bounds__(256) main_f32_packed(MainParams<RecF32, float>
 template <int K>
 __global__ void __launch_bounds__(256) main_f32_packed_gls(MainParams<RecF32, float> p) {
   constexpr int F = 2 * K;
-  __shared__ uint4 s_obs[2 * LSP_TILE_OBS];
+  __shared__ ObsF2W s_ent[LSP_TILE_OBS];
+  __shared__ uint32_t s_bal[LSP_TILE_OBS / 32];
   __shared__ unsigned long long red[32];
   __shared__ uint32_t s_item;
   extern __shared__ __align__(16) unsigned char dyn_smem[];
@@ -254,7 +409,6 @@ __global__ void __launch_bounds__(256) main_f32_packed_gls(MainParams<RecF32, fl
     const ObjInfo oi = p.obj[o];
     const int64_t kc0 = (int64_t)chunk * blockDim.x * F;
     const uint32_t k0 = (uint32_t)(kc0 + (int64_t)tid * F);
-    const uint32_t k1 = k0 + K;
     const int64_t ob = oi.begin;
     const int64_t oe = oi.flags ? ob : oi.begin + oi.n;
 
@@ -264,36 +418,26 @@ __global__ void __launch_bounds__(256) main_f32_packed_gls(MainParams<RecF32, fl
 
     for (int64_t ts = ob; ts < oe; ts += LSP_TILE_OBS) {
       const int nt = (int)((oe - ts) < LSP_TILE_OBS ? (oe - ts) : LSP_TILE_OBS);
-      const uint4* src = reinterpret_cast<const uint4*>(p.rec + ts);
-      for (int i = tid; i < 2 * nt; i += blockDim.x) s_obs[i] = __ldg(src + i);
-      __syncthreads();
-      for (int j = 0; j < nt; ++j) {
-        const uint4 r0 = s_obs[2 * j];
-        const uint4 r1 = s_obs[2 * j + 1];
+      const int n_ch = stage_tile(reinterpret_cast<const uint4*>(p.rec + ts), nt, (uint32_t)K, s_ent, s_bal);
+      auto obs = [&](const ObsF2W& ew, auto cheb_tag) {
+        const ObsF2& e = ew.e;
         f2_t c2, s2;
-        seed_pair(make_uint4(r0.w, r1.x, r1.y, 0u), k0, k1, c2, s2);
-        const f2_t u2 = f2_of(r0.x, r0.x), w2 = f2_of(r1.w, r1.w);
-        const f2_t cr2 = f2_of(r0.y, r0.y), sr2 = f2_of(r0.z, r0.z);
-        const uint32_t nsr = r0.z ^ 0x80000000u;
-        const f2_t nsr2 = f2_of(nsr, nsr);
-#pragma unroll
-        for (int m = 0; m < K; ++m) {
-          xc[m] = f2_fma(u2, c2, xc[m]);
-          xs[m] = f2_fma(u2, s2, xs[m]);
-          cw[m] = f2_fma(w2, c2, cw[m]);
-          sw[m] = f2_fma(w2, s2, sw[m]);
-          const f2_t wc = f2_mul(w2, c2);
-          cc[m] = f2_fma(wc, c2, cc[m]);
-          cs[m] = f2_fma(wc, s2, cs[m]);
-          if (m + 1 < K) {
-            const f2_t tc = f2_mul(c2, cr2);
-            const f2_t tsr = f2_mul(s2, cr2);
-            const f2_t cn = f2_fma(s2, nsr2, tc);
-            s2 = f2_fma(c2, sr2, tsr);
-            c2 = cn;
-          }
-        }
-      }
+        seed_pair_kb(e, k0, c2, s2);
+        const f2_t u2 = e.y, nu2 = e.ny, w2 = ew.w, nw2 = ew.nw;
+        chain3_mode<K, decltype(cheb_tag)::value>(c2, s2, e.cr, e.sr, e.nsr, e.coef, e.ncoef,
+                                                  [&](int m, bool neg, f2_t c, f2_t s) {
+                                                    const f2_t uu = neg ? nu2 : u2, ww = neg ? nw2 : w2;
+                                                    xc[m] = f2_fma(uu, c, xc[m]);
+                                                    xs[m] = f2_fma(uu, s, xs[m]);
+                                                    cw[m] = f2_fma(ww, c, cw[m]);
+                                                    sw[m] = f2_fma(ww, s, sw[m]);
+                                                    const f2_t wc = f2_mul(w2, c);
+                                                    cc[m] = f2_fma(wc, c, cc[m]);
+                                                    cs[m] = f2_fma(wc, s, cs[m]);
+                                                  });
+      };
+      for (int j = 0; j < n_ch; ++j) obs(s_ent[j], std::true_type{});
+      for (int j = n_ch; j < nt; ++j) obs(s_ent[j], std::false_type{});
       __syncthreads();
     }
 
@@ -365,22 +509,17 @@ __global__ void __launch_bounds__(256) main_f64_gls(MainParams<RecF64, double> p
         const RecF64 r = srec[j];
         double c, s;
         seed_sincos_f64(r.a + (uint64_t)k0 * r.b, c, s);
-        const double u = r.y, w = __longlong_as_double((long long)r.pad), cr = r.cr, sr = r.sr;
-#pragma unroll
-        for (int m = 0; m < K; ++m) {
-          xc[m] = fma(u, c, xc[m]);
-          xs[m] = fma(u, s, xs[m]);
-          cw[m] = fma(w, c, cw[m]);
-          sw[m] = fma(w, s, sw[m]);
-          const double wc = w * c;
-          cc[m] = fma(wc, c, cc[m]);
-          cs[m] = fma(wc, s, cs[m]);
-          if (m + 1 < K) {
-            const double cn = fma(-s, sr, c * cr);
-            s = fma(c, sr, s * cr);
-            c = cn;
-          }
-        }
+        const double u = r.y, w = __longlong_as_double((long long)r.pad), nu = neg_(u), nw = neg_(w);
+        chain3<K>(c, s, r.cr, r.sr, sin_dominates(r.cr, r.sr), [&](int m, bool neg, double cm, double sm) {
+          const double uu = neg ? nu : u, ww = neg ? nw : w;
+          xc[m] = fma(uu, cm, xc[m]);
+          xs[m] = fma(uu, sm, xs[m]);
+          cw[m] = fma(ww, cm, cw[m]);
+          sw[m] = fma(ww, sm, sw[m]);
+          const double wc = w * cm;
+          cc[m] = fma(wc, cm, cc[m]);
+          cs[m] = fma(wc, sm, cs[m]);
+        });
       }
       __syncthreads();
     }
@@ -445,19 +584,19 @@ __global__ void __launch_bounds__(256) main_scalar(MainParams<Rec, Real> p) {
         } else {
           seed_sincos_f64(r.a + (uint64_t)k0 * r.b, c, s);
         }
-        const Real y = r.y, cr = r.cr, sr = r.sr;
-#pragma unroll
-        for (int m = 0; m < K; ++m) {
-          xc[m] = fma(y, c, xc[m]);
-          xs[m] = fma(y, s, xs[m]);
-          cc[m] = fma(c, c, cc[m]);
-          cs[m] = fma(c, s, cs[m]);
-          if (m + 1 < K) {
-            const Real cn = fma(-s, sr, c * cr);
-            s = fma(c, sr, s * cr);
-            c = cn;
-          }
-        }
+        const Real y = r.y, ny = neg_(y);
+        bool cheb;
+        if constexpr (std::is_same<Real, float>::value)
+          cheb = sin_dominates(__float_as_uint(r.cr), __float_as_uint(r.sr));
+        else
+          cheb = sin_dominates(r.cr, r.sr);
+        chain3<K>(c, s, (Real)r.cr, (Real)r.sr, cheb, [&](int m, bool neg, Real cm, Real sm) {
+          const Real yy = neg ? ny : y;
+          xc[m] = fma(yy, cm, xc[m]);
+          xs[m] = fma(yy, sm, xs[m]);
+          cc[m] = fma(cm, cm, cc[m]);
+          cs[m] = fma(cm, sm, cs[m]);
+        });
       }
       __syncthreads();
     }

@@ -186,6 +186,18 @@ def test_batch_top3(env, small_batch, precision):
             assert abs(pk["power"][o, r] - ref[precision]["top_pow"][o, r]) <= tol * 2
 
 
+def test_batch_top3_every_variant(env, small_batch):
+    # top-3 adds a per-CTA candidate buffer in dynamic shared memory; with
+    # the largest tiles (K 16, 256 threads) static + dynamic exceed 48 KB
+    b, ref = small_batch
+    for var in FP32_VARIANTS:
+        _, pk = batch(env, b, "fp32", top_k=3, **var)
+        pk = pk.reshape(b.n_obj, 3)
+        for o in range(b.n_obj):
+            for r in range(3):
+                assert abs(pk["power"][o, r] - ref["fp32"]["top_pow"][o, r]) <= 2 * TOL32, (var, o, r)
+
+
 def test_fused_argmax_matches_own_power(env, small_batch):
     # integer decision in the kernel's own precision: bit-exact
     b, _ = small_batch
