@@ -38,8 +38,10 @@ sys.path.insert(0, ROOT)
 import synth  # noqa: E402
 
 METRIC = "objects/sec and trig-sum evals/s (N_t*N_f) vs FP32 roofline; learned vs plain"
-OPS_PER_PAIR = 6           # 2 FFMA (three-term recurrence step) + 4 FFMA (XC, XS, CC, CS); a chain of K
-                           # pairs spends 4 on its one rotation and 2 (K - 2) on three-term steps: 6K in all
+OPS_PER_PAIR = 8           # roofline work unit: one pair in the rotation-recurrence form costs 2 FMUL +
+                           # 2 FFMA (rotation) + 4 FFMA (XC, XS, CC, CS) on the FP32 pipe
+KERNEL_OPS_PER_PAIR = 6    # what the kernels spend: a chain of K pairs takes one rotation (4) and K - 2
+                           # three-term steps (2 each), 2K in all, plus the 4 FFMA of the sums
 FP32_LANES_PER_SM = 128    # FP32 lanes per SM per clock
 FP64_LANES_PER_SM = 2      # FP64 FMAs per SM per clock: 1.25 TFLOP/s nominal / (2 x 152 SMs x 2.07 GHz)
 
@@ -331,8 +333,15 @@ def run_gpu(args, w, name):
     achieved = pairs / (main_avg / 1e3) / 1e9
     clk_mhz = (clocks or {}).get("sm_mhz") or 0.0
     lanes = FP64_LANES_PER_SM if fp64 else FP32_LANES_PER_SM
-    peak = n_sm * lanes * clk_mhz * 1e6 / OPS_PER_PAIR / 1e9 if clk_mhz else None
+    rates = lsp.probe_fma_rates(dev)  # measured pipe ceilings, outside the timed region
+    if fp64:  # FP64: against the measured DFMA rate
+        peak = rates["f64"] / OPS_PER_PAIR / 1e9
+        basis = f"measured DFMA rate {rates['f64'] / 1e9:.0f} G/s (register-only probe) / {OPS_PER_PAIR} ops per pair"
+    else:     # FP32: nominal lanes at the sampled SM clock
+        peak = n_sm * lanes * clk_mhz * 1e6 / OPS_PER_PAIR / 1e9 if clk_mhz else None
+        basis = f"{n_sm} SMs x {lanes} FP32 lanes x sampled SM clock / {OPS_PER_PAIR} ops per pair"
     peak_max = n_sm * lanes * 2070e6 / OPS_PER_PAIR / 1e9
+    ceiling = (rates["f64"] if fp64 else rates["f32x2"]) / OPS_PER_PAIR / 1e9
     src = source_hash()
     traffic = recorded_traffic(name, src)
 
@@ -352,9 +361,13 @@ def run_gpu(args, w, name):
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gpair/s",
                          "frac": (achieved / peak) if peak else None, "traffic": traffic,
                          "kernel": "main trig-sum kernel", "main_kernel_ms": main_avg,
-                         "peak_basis": f"{n_sm} SMs x {lanes} {'FP64' if fp64 else 'FP32'} lanes x sampled SM "
-                                       f"clock / {OPS_PER_PAIR} ops per pair",
-                         "peak_at_max_clock": peak_max, "source_hash": src},
+                         "peak_basis": basis, "peak_nominal_at_max_clock": peak_max,
+                         "measured_fma_rates_per_s": rates,
+                         "frac_of_measured_pipe_ceiling": achieved / ceiling,
+                         "kernel_ops_per_pair": KERNEL_OPS_PER_PAIR,
+                         "pipe_busy_with_kernel_ops": (achieved * KERNEL_OPS_PER_PAIR / OPS_PER_PAIR / peak)
+                         if (peak and not fp64) else achieved * KERNEL_OPS_PER_PAIR / OPS_PER_PAIR / ceiling,
+                         "source_hash": src},
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": "objects/s", "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(d2h), "ms_per_step": statistics.mean(e2e_ms)},

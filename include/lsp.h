@@ -380,6 +380,20 @@ lsp_status lsp_refine_windows(const double* t, const float* y, const int64_t* of
                               int32_t inconclusive_fallback, lsp_peak* peaks, int32_t* info,
                               void* workspace, size_t ws_bytes, lsp_stream_t stream);
 
+/*
+ * Calibration probe of the FMA pipes (no counterpart in the paper): runs
+ * register-only kernels of independent FMA chains (scalar FP32, packed
+ * f32x2, FP64) on the current device, 64 warps per SM, and writes the
+ * sustained rate of each in FMA lane-operations per second for the whole
+ * device (a packed FMA counts two).  These are the ceilings the trig-sum
+ * kernels' FP32 and FP64 fractions are read against.  Takes a few tens of
+ * milliseconds, synchronizes `stream`, and allocates and frees a small
+ * device buffer (one float per probe thread).  Outputs are host pointers,
+ * each nullable.  Errors: LSP_E_CUDA (message in lsp_last_error).
+ */
+lsp_status lsp_probe_fma_rates(double* f32_per_s, double* f32x2_per_s, double* f64_per_s,
+                               lsp_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -81,6 +81,7 @@ EXPORTS = [
     "lsp_mlp_param_count", "lsp_mlp_workspace_size", "lsp_featurize", "lsp_mlp_forward",
     "lsp_mlp_loss_grad", "lsp_mlp_adamw", "lsp_to_bf16", "lsp_top_classes", "lsp_refine_workspace_size",
     "lsp_refine_windows", "lsp_batch_gls", "lsp_periodogram_gls", "lsp_workspace_size_gls",
+    "lsp_probe_fma_rates",
 ]
 
 
@@ -200,6 +201,20 @@ def grid_for_span(f_min: float, f_max: float, t_span: float) -> Grid:
     g = Grid()
     _check(lib().lsp_grid_for_span(float(f_min), float(f_max), float(t_span), ctypes.byref(g)))
     return g
+
+
+def probe_fma_rates(device=None) -> dict:
+    """Measured FMA-pipe rates of the current GPU, in lane-operations per second
+    for the whole device: scalar FP32, packed f32x2 (two per instruction) and
+    FP64.  Register-only probe kernels in the library; the ceilings for the
+    trig-sum kernels' roofline fractions."""
+    import torch
+    dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+    r32, r2, r64 = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    with torch.cuda.device(dev):
+        _check(lib().lsp_probe_fma_rates(ctypes.byref(r32), ctypes.byref(r2), ctypes.byref(r64),
+                                         _stream_handle(dev)))
+    return {"f32": r32.value, "f32x2": r2.value, "f64": r64.value}
 
 
 def workspace_size(n_obj, total_nt, grid: Grid, opts: Opts) -> int:

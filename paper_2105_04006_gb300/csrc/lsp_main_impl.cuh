@@ -200,19 +200,19 @@ __device__ __forceinline__ void chain3(T c, T s, T cr, T sr, bool cheb, Body&& b
 // ------------------------------------------------ expanded observation tile
 // The packed kernels stage each tile of observations into shared memory as
 // ObsF2 entries that hold every operand of the inner loop already paired for
-// f32x2 and already negated, with the tile's Chebyshev observations first
+// f32x2 (negated where a negation is needed), with the tile's Chebyshev observations first
 // and its leapfrog observations after them (a stable partition by index,
 // so the summation order is fixed).  The inner loops then issue no packing,
 // sign or mode instructions and no per-observation branch.
 struct __align__(16) ObsF2 {
-  f2_t y, ny;         // {y, y}, {-y, -y}  (GLS: u = w (y - ybar_w))
+  f2_t y;             // {y, y}  (GLS: u = w (y - ybar_w))
   f2_t cr, sr, nsr;   // cos, sin and -sin of the grid step angle theta
   f2_t coef, ncoef;   // +-2 cos theta (Chebyshev) or +-2 sin theta (leapfrog)
   uint32_t a_hi, b_hi, b_lo, kb_hi;  // phase words and the high word of K b
 };
 struct __align__(16) ObsF2W {
   ObsF2 e;
-  f2_t w, nw;         // {w, w}, {-w, -w}, w = 1 / dy^2 (generalized periodogram)
+  f2_t w, nu, nw;     // {w, w} with w = 1 / dy^2, {-u, -u}, {-w, -w} (generalized periodogram)
 };
 
 __device__ __forceinline__ f2_t f2_dup(uint32_t v) { return f2_of(v, v); }
@@ -221,7 +221,6 @@ __device__ __forceinline__ void expand_obs(const uint4 r0, const uint4 r1, bool 
   const uint32_t sign = 0x80000000u;
   const uint32_t cf = cheb ? r0.y + 0x00800000u : r0.z + 0x00800000u;  // 2 cr or 2 sr (exponent + 1)
   e.y = f2_dup(r0.x);
-  e.ny = f2_dup(r0.x ^ sign);
   e.cr = f2_dup(r0.y);
   e.sr = f2_dup(r0.z);
   e.nsr = f2_dup(r0.z ^ sign);
@@ -235,6 +234,7 @@ __device__ __forceinline__ void expand_obs(const uint4 r0, const uint4 r1, bool 
 __device__ __forceinline__ void expand_obs(const uint4 r0, const uint4 r1, bool cheb, uint32_t K, ObsF2W& e) {
   expand_obs(r0, r1, cheb, K, e.e);
   e.w = f2_dup(r1.w);
+  e.nu = f2_dup(r0.x ^ 0x80000000u);
   e.nw = f2_dup(r1.w ^ 0x80000000u);
 }
 
@@ -323,20 +323,35 @@ __global__ void __launch_bounds__(256) main_f32_packed(MainParams<RecF32, float>
     for (int64_t ts = ob; ts < oe; ts += LSP_TILE_OBS) {
       const int nt = (int)((oe - ts) < LSP_TILE_OBS ? (oe - ts) : LSP_TILE_OBS);
       const int n_ch = stage_tile(reinterpret_cast<const uint4*>(p.rec + ts), nt, (uint32_t)K, s_ent, s_bal);
+      // The Chebyshev values carry sigma_m; rather than alternate y and -y (a
+      // measured 10 % loss of FMA throughput), the y-weighted sums of the
+      // sigma_m = -1 frequencies are negated around the Chebyshev run, which
+      // is exact: the sums come out bit-identical.
       auto obs = [&](const ObsF2& e, auto cheb_tag) {
         f2_t c2, s2;
         seed_pair_kb(e, k0, c2, s2);
-        const f2_t y2 = e.y, ny2 = e.ny;
+        const f2_t y2 = e.y;
         chain3_mode<K, decltype(cheb_tag)::value>(c2, s2, e.cr, e.sr, e.nsr, e.coef, e.ncoef,
-                                                  [&](int m, bool neg, f2_t c, f2_t s) {
-                                                    const f2_t yy = neg ? ny2 : y2;
-                                                    xc[m] = f2_fma(yy, c, xc[m]);
-                                                    xs[m] = f2_fma(yy, s, xs[m]);
+                                                  [&](int m, bool, f2_t c, f2_t s) {
+                                                    xc[m] = f2_fma(y2, c, xc[m]);
+                                                    xs[m] = f2_fma(y2, s, xs[m]);
                                                     cc[m] = f2_fma(c, c, cc[m]);
                                                     cs[m] = f2_fma(c, s, cs[m]);
                                                   });
       };
-      for (int j = 0; j < n_ch; ++j) obs(s_ent[j], std::true_type{});
+      auto flip = [&]() {
+#pragma unroll
+        for (int m = 0; m < K; ++m)
+          if (m & 2) {
+            xc[m] = neg_(xc[m]);
+            xs[m] = neg_(xs[m]);
+          }
+      };
+      if (n_ch > 0) {
+        flip();
+        for (int j = 0; j < n_ch; ++j) obs(s_ent[j], std::true_type{});
+        flip();
+      }
       for (int j = n_ch; j < nt; ++j) obs(s_ent[j], std::false_type{});
       __syncthreads();
     }
@@ -423,7 +438,7 @@ __global__ void __launch_bounds__(256) main_f32_packed_gls(MainParams<RecF32, fl
         const ObsF2& e = ew.e;
         f2_t c2, s2;
         seed_pair_kb(e, k0, c2, s2);
-        const f2_t u2 = e.y, nu2 = e.ny, w2 = ew.w, nw2 = ew.nw;
+        const f2_t u2 = e.y, nu2 = ew.nu, w2 = ew.w, nw2 = ew.nw;
         chain3_mode<K, decltype(cheb_tag)::value>(c2, s2, e.cr, e.sr, e.nsr, e.coef, e.ncoef,
                                                   [&](int m, bool neg, f2_t c, f2_t s) {
                                                     const f2_t uu = neg ? nu2 : u2, ww = neg ? nw2 : w2;
@@ -436,6 +451,8 @@ __global__ void __launch_bounds__(256) main_f32_packed_gls(MainParams<RecF32, fl
                                                     cs[m] = f2_fma(wc, s, cs[m]);
                                                   });
       };
+      // (the accumulator flip of main_f32_packed costs this kernel registers
+      // and occupancy: here the weights alternate sign instead)
       for (int j = 0; j < n_ch; ++j) obs(s_ent[j], std::true_type{});
       for (int j = n_ch; j < nt; ++j) obs(s_ent[j], std::false_type{});
       __syncthreads();

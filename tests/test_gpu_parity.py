@@ -481,3 +481,15 @@ def test_periodogram_written_to_pinned_host_memory(env, small_batch):
     plan.execute_host(b.t, b.y.astype(np.float32), b.offsets, power=host3)
     np.testing.assert_array_equal(host3, p_dev.cpu().numpy())
     plan.close()
+
+
+def test_fma_rate_probe_is_plausible(env):
+    # ceilings for the roofline fractions: below the nominal unit counts at the
+    # highest SM clock of the part (2.07 GHz), and not far below them
+    lsp, torch, dev = env
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    r = lsp.probe_fma_rates(dev)
+    f32_nominal = n_sm * 128 * 2.07e9
+    assert 0.5 * f32_nominal < r["f32"] <= 1.02 * f32_nominal, r
+    assert 0.5 * f32_nominal < r["f32x2"] <= 1.02 * f32_nominal, r
+    assert 0.3 * n_sm * 2 * 2.07e9 < r["f64"] <= 1.02 * n_sm * 2 * 2.07e9, r
