@@ -347,12 +347,17 @@ __global__ void __launch_bounds__(256) main_f32_packed(MainParams<RecF32, float>
             xs[m] = neg_(xs[m]);
           }
       };
-      if (n_ch > 0) {
-        flip();
-        for (int j = 0; j < n_ch; ++j) obs(s_ent[j], std::true_type{});
-        flip();
+      // threads whose bins all lie past the end of the grid (the ragged last
+      // chunk) only help stage tiles; a warp of them leaves its FMA pipe to
+      // the other CTAs on the SM
+      if ((int64_t)k0 < kend) {
+        if (n_ch > 0) {
+          flip();
+          for (int j = 0; j < n_ch; ++j) obs(s_ent[j], std::true_type{});
+          flip();
+        }
+        for (int j = n_ch; j < nt; ++j) obs(s_ent[j], std::false_type{});
       }
-      for (int j = n_ch; j < nt; ++j) obs(s_ent[j], std::false_type{});
       __syncthreads();
     }
 
@@ -453,8 +458,10 @@ __global__ void __launch_bounds__(256) main_f32_packed_gls(MainParams<RecF32, fl
       };
       // (the accumulator flip of main_f32_packed costs this kernel registers
       // and occupancy: here the weights alternate sign instead)
-      for (int j = 0; j < n_ch; ++j) obs(s_ent[j], std::true_type{});
-      for (int j = n_ch; j < nt; ++j) obs(s_ent[j], std::false_type{});
+      if ((int64_t)k0 < p.n_f) {  // bins past the grid end: staging only
+        for (int j = 0; j < n_ch; ++j) obs(s_ent[j], std::true_type{});
+        for (int j = n_ch; j < nt; ++j) obs(s_ent[j], std::false_type{});
+      }
       __syncthreads();
     }
 
@@ -522,7 +529,8 @@ __global__ void __launch_bounds__(256) main_f64_gls(MainParams<RecF64, double> p
       const uint4* src = reinterpret_cast<const uint4*>(p.rec + ts);
       for (int i = tid; i < 3 * nt; i += blockDim.x) s_rec[i] = __ldg(src + i);
       __syncthreads();
-      for (int j = 0; j < nt; ++j) {
+      const int nt_c = (int64_t)k0 < p.n_f ? nt : 0;  // bins past the grid end: staging only
+      for (int j = 0; j < nt_c; ++j) {
         const RecF64 r = srec[j];
         double c, s;
         seed_sincos_f64(r.a + (uint64_t)k0 * r.b, c, s);
@@ -593,7 +601,8 @@ __global__ void __launch_bounds__(256) main_scalar(MainParams<Rec, Real> p) {
       const uint4* src = reinterpret_cast<const uint4*>(p.rec + ts);
       for (int i = tid; i < RW * nt; i += blockDim.x) s_rec[i] = __ldg(src + i);
       __syncthreads();
-      for (int j = 0; j < nt; ++j) {
+      const int nt_c = (int64_t)k0 < p.n_f ? nt : 0;  // bins past the grid end: staging only
+      for (int j = 0; j < nt_c; ++j) {
         const Rec r = srec[j];
         Real c, s;
         if constexpr (std::is_same<Real, float>::value) {
