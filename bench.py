@@ -236,6 +236,36 @@ def run_reference(args, w, name):
 
 
 # --------------------------------------------------------------- GPU arm
+def run_ablations(args, lsp, torch, plan, b, t, y, off, name, rank):
+    """The paper's kernel comparisons on GB300 through the autotuner: every candidate
+    configuration, including the ablation kernels (per-pair SFU or accurate sin/cos
+    instead of the recurrence; observations read from global memory instead of shared
+    memory tiles), timed on this workload and checked against the FP64 path."""
+    import tempfile
+    clocks_s = ClockSampler(os.environ.get("CUDA_VISIBLE_DEVICES", str(t.device.index or 0)).split(",")[0])
+    clocks_s.start()
+    clocks_s.mark(0)
+    with tempfile.TemporaryDirectory() as td:
+        cfg, trials = plan.autotune(t, y, off, cache_path=os.path.join(td, "tune.jsonl"), ablations=True,
+                                    return_trials=True)
+    clocks_s.mark(1)
+    clocks = clocks_s.stop()
+    pairs = b.pairs
+    rows = []
+    for tr in trials:
+        c = tr["config"]
+        kind = ("recurrence", "SFU sincos per pair", "accurate sincospif per pair")[c["trig"]]
+        rows.append({"config": c, "trig": kind, "staging": ("shared", "global")[c["staging"]],
+                     "ms_per_step": tr["ms"], "pairs_per_s": pairs / (tr["ms"] * 1e-3) if tr["ms"] > 0 else None,
+                     "max_err_vs_fp64": tr["max_err"], "passed_gate": tr["passed"]})
+    plan.close()
+    if rank == 0:
+        print(json.dumps({"impl": "gb300", "mode": "ablations", "workload": name, "n_obj": b.n_obj,
+                          "total_nt": int(b.t.size), "n_f": b.grid.n_f, "chosen": cfg, "trials": rows,
+                          "clocks": clocks}), flush=True)
+    return 0
+
+
 def run_gpu(args, w, name):
     import torch
     import paper_2105_04006_gb300 as lsp
@@ -258,8 +288,10 @@ def run_gpu(args, w, name):
     power = (torch.empty((b.n_obj, g.n_f), dtype=torch.float64 if fp64 else torch.float32, device=dev)
              if w["power"] else None)
     plan = lsp.Plan(b.n_obj, b.t.size, g, top_k=w["top_k"], precision=args.precision)
+    if args.ablations:
+        return run_ablations(args, lsp, torch, plan, b, t, y, off, name, rank)
     if args.config:
-        keys = ("k_reseed", "freqs_per_thread", "block_threads", "obs_split", "packed")
+        keys = ("k_reseed", "freqs_per_thread", "block_threads", "obs_split", "packed", "trig", "staging")
         plan.set_config(**dict(zip(keys, (int(v) for v in args.config.split(",")))))
     elif not args.no_tune:
         cache = os.path.join(ROOT, "paper_2105_04006_gb300", "_build", "tune_cache.jsonl")
@@ -469,7 +501,11 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
     ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
     ap.add_argument("--config", default=None,
-                    help="force a kernel configuration: k_reseed,freqs_per_thread,block_threads,obs_split,packed")
+                    help="force a kernel configuration: k_reseed,freqs_per_thread,block_threads,obs_split,packed"
+                         "[,trig,staging]")
+    ap.add_argument("--ablations", action="store_true",
+                    help="time every autotuner candidate, including the trig/staging ablation kernels, and print "
+                         "them (one JSON line) instead of the benchmark")
     ap.add_argument("--n-obj", type=int, default=None,
                     help="objects in a batch workload (default: the workload's own count)")
     args = ap.parse_args()

@@ -218,14 +218,30 @@ lsp_status lsp_argmax_period(const void* power, int64_t n_obj, int64_t n_f, cons
 
 typedef struct lsp_plan lsp_plan;
 
-/* The launch configuration a plan uses (see lsp_plan_autotune). */
+/*
+ * The launch configuration a plan uses (see lsp_plan_autotune).  trig and
+ * staging select the ablation kernels of the paper's own comparisons
+ * (Section 3.6 and Table 3: observations staged in shared memory or read
+ * from global memory; Section 4.12 and Table 6: fast or accurate sin/cos) and
+ * are 0 in every configuration the library picks by itself:
+ *   trig     0: reseeded recurrence (default);
+ *            1: every pair's (cos, sin) from the SFU intrinsic of its exact phase;
+ *            2: every pair's (cos, sin) from the accurate sincospif;
+ *   staging  0: observation tiles in shared memory (default);
+ *            1: every thread reads each observation record from global memory.
+ * The ablation kernels (trig or staging non-zero) are FP32, scalar
+ * (packed 0), k_reseed = freqs_per_thread = 16, standard periodogram only;
+ * other combinations return LSP_E_UNSUPPORTED.
+ */
 typedef struct lsp_config {
   int32_t k_reseed;
   int32_t freqs_per_thread;
   int32_t block_threads;
   int32_t obs_split;
   int32_t packed;      /* 1: packed f32x2 arithmetic across two reseed chains */
-  int32_t reserved[3];
+  int32_t trig;
+  int32_t staging;
+  int32_t reserved;
 } lsp_config;
 
 /*
@@ -262,13 +278,38 @@ lsp_status lsp_plan_execute_host(lsp_plan* plan, const double* t, const void* y,
 /*
  * Measure the candidate launch configurations on these inputs, keep the
  * fastest one whose powers stay within the FP32 error gate (1e-4 absolute
- * in P_n, against the FP64 path on sampled frequencies), and use it from
- * now on.  Synchronises `stream`.  When cache_path is not NULL the choice
- * is read from / appended to that JSON-lines file, keyed by device, shape
- * class and options.
+ * in P_n: the first object's periodogram against the FP64 path), and use it
+ * from now on.  Synchronises `stream`.  When cache_path is not NULL the
+ * choice is read from / appended to that JSON-lines file, keyed by device,
+ * shape class and options.
  */
 lsp_status lsp_plan_autotune(lsp_plan* plan, const double* t, const void* y, const int64_t* offsets,
                              const char* cache_path, lsp_stream_t stream);
+
+/* One candidate measured by lsp_plan_autotune_ex. */
+typedef struct lsp_trial {
+  lsp_config config;
+  float ms;          /* time of one execution (mean of 3 graph replays), ms; -1 if not timed */
+  float max_err;     /* max |P_n - P_n(FP64)| on the first object (0 for FP64 plans) */
+  int32_t passed;    /* 1: within the error gate, so eligible (failed candidates are not timed) */
+  int32_t reserved;
+} lsp_trial;
+
+#define LSP_TUNE_ABLATIONS 1  /* also measure the trig/staging ablation kernels (lsp_config) */
+
+/*
+ * lsp_plan_autotune with a record of what it measured.  flags: 0 or
+ * LSP_TUNE_ABLATIONS (the ablation kernels join the candidates; they win only
+ * where they are faster).  trials (host array, nullable) receives the first
+ * max_trials of the measured candidates in the order measured and
+ * *n_trials (nullable) their number.  With LSP_TUNE_ABLATIONS the cache is
+ * not consulted (every candidate is measured); the choice is still appended
+ * to it.  lsp_plan_autotune(...) is lsp_plan_autotune_ex(..., 0, NULL, 0,
+ * NULL, stream).
+ */
+lsp_status lsp_plan_autotune_ex(lsp_plan* plan, const double* t, const void* y, const int64_t* offsets,
+                                const char* cache_path, int32_t flags, lsp_trial* trials,
+                                int32_t max_trials, int32_t* n_trials, lsp_stream_t stream);
 
 /*
  * Timing probe.  While enabled, each execution of the plan also records two

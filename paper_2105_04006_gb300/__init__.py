@@ -62,11 +62,21 @@ class Opts(ctypes.Structure):
 class Config(ctypes.Structure):
     _fields_ = [("k_reseed", ctypes.c_int32), ("freqs_per_thread", ctypes.c_int32),
                 ("block_threads", ctypes.c_int32), ("obs_split", ctypes.c_int32),
-                ("packed", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+                ("packed", ctypes.c_int32), ("trig", ctypes.c_int32), ("staging", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
     def as_dict(self):
         return dict(k_reseed=self.k_reseed, freqs_per_thread=self.freqs_per_thread,
-                    block_threads=self.block_threads, obs_split=self.obs_split, packed=self.packed)
+                    block_threads=self.block_threads, obs_split=self.obs_split, packed=self.packed,
+                    trig=self.trig, staging=self.staging)
+
+
+class Trial(ctypes.Structure):
+    _fields_ = [("config", Config), ("ms", ctypes.c_float), ("max_err", ctypes.c_float),
+                ("passed", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+TUNE_ABLATIONS = 1
 
 
 _lib = None
@@ -81,7 +91,7 @@ EXPORTS = [
     "lsp_mlp_param_count", "lsp_mlp_workspace_size", "lsp_featurize", "lsp_mlp_forward",
     "lsp_mlp_loss_grad", "lsp_mlp_adamw", "lsp_to_bf16", "lsp_top_classes", "lsp_refine_workspace_size",
     "lsp_refine_windows", "lsp_batch_gls", "lsp_periodogram_gls", "lsp_workspace_size_gls",
-    "lsp_probe_fma_rates",
+    "lsp_probe_fma_rates", "lsp_plan_autotune_ex",
 ]
 
 
@@ -120,6 +130,7 @@ def lib():
             L.lsp_plan_execute.argtypes = [P, P, P, P, P, P, P]
             L.lsp_plan_execute_host.argtypes = [P, P, P, P, P, P, P]
             L.lsp_plan_autotune.argtypes = [P, P, P, P, ctypes.c_char_p, P]
+            L.lsp_plan_autotune_ex.argtypes = [P, P, P, P, ctypes.c_char_p, i32, P, i32, P, P]
             L.lsp_plan_get_config.argtypes = [P, ctypes.POINTER(Config)]
             L.lsp_plan_set_config.argtypes = [P, ctypes.POINTER(Config)]
             L.lsp_plan_enable_timing.argtypes = [P, i32]
@@ -425,11 +436,23 @@ class Plan:
                                            _stream_handle(dev)))
         return peaks
 
-    def autotune(self, t, y, offsets=None, cache_path=None):
+    def autotune(self, t, y, offsets=None, cache_path=None, ablations=False, return_trials=False):
+        """Pick the fastest configuration within the FP32 error gate.  ablations:
+        also measure the trig/staging ablation kernels.  return_trials: return
+        (config, [trial dicts]) with every measured candidate."""
         torch = _torch()
         _require(t, "t", torch.float64)
         _require(y, "y", _dtypes(self.opts), t.device)
         cp = cache_path.encode() if cache_path else None
-        _check(lib().lsp_plan_autotune(self._h, _ptr(t), _ptr(y), _ptr(offsets), cp,
-                                       _stream_handle(t.device)))
-        return self.config
+        if not (ablations or return_trials):
+            _check(lib().lsp_plan_autotune(self._h, _ptr(t), _ptr(y), _ptr(offsets), cp,
+                                           _stream_handle(t.device)))
+            return self.config
+        buf = (Trial * 64)()
+        n = ctypes.c_int32(0)
+        _check(lib().lsp_plan_autotune_ex(self._h, _ptr(t), _ptr(y), _ptr(offsets), cp,
+                                          TUNE_ABLATIONS if ablations else 0, buf, 64, ctypes.byref(n),
+                                          _stream_handle(t.device)))
+        trials = [dict(config=buf[i].config.as_dict(), ms=float(buf[i].ms), max_err=float(buf[i].max_err),
+                       passed=bool(buf[i].passed)) for i in range(min(n.value, 64))]
+        return (self.config, trials) if return_trials else self.config

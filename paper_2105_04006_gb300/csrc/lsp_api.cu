@@ -65,6 +65,7 @@ int current_sm_count() {
 // Resolved configuration and workspace layout of one call.
 struct Layout {
   int prec, packed, k, fpt, threads, split, top_k, top, norm, center, gls;
+  int abl = 0;  // ablation kernel code (lsp_config trig + 3 * staging)
   int64_t n_obj, total_nt, n_f;
   double f_min, df;
   int32_t n_chunks, n_res_chunks;
@@ -116,13 +117,16 @@ lsp_status resolve(int64_t n_obj, int64_t total_nt, const lsp_grid* g, const lsp
   l.df = (g->f_max - g->f_min) / (double)g->n_f;
   l.gls = gls ? 1 : 0;
 
-  int k, fpt, threads, packed, split_req;
+  int k, fpt, threads, packed, split_req, abl = 0;
   if (cfg) {
     k = cfg->k_reseed;
     fpt = cfg->freqs_per_thread;
     threads = cfg->block_threads;
     packed = cfg->packed;
     split_req = cfg->obs_split;
+    if (cfg->trig < 0 || cfg->trig > 2 || cfg->staging < 0 || cfg->staging > 1)
+      return fail(LSP_E_ARG, "trig must be 0, 1 or 2 and staging 0 or 1");
+    abl = cfg->trig + 3 * cfg->staging;
   } else {
     k = o.k_reseed ? o.k_reseed : 8;
     if (l.prec == LSP_FP64) {
@@ -140,9 +144,12 @@ lsp_status resolve(int64_t n_obj, int64_t total_nt, const lsp_grid* g, const lsp
   }
   if (threads < 64 || threads > 256 || threads % 32)
     return fail(LSP_E_ARG, "block_threads must be a multiple of 32 in [64, 256]");
-  if (!main_variant_exists(l.prec, packed, k, fpt, l.gls))
-    return fail(LSP_E_UNSUPPORTED, "no %skernel for precision %d with k_reseed=%d, freqs_per_thread=%d",
-                gls ? "generalized " : "", l.prec, k, fpt);
+  if (!main_variant_exists(l.prec, packed, k, fpt, l.gls, abl))
+    return fail(LSP_E_UNSUPPORTED,
+                "no %skernel for precision %d with k_reseed=%d, freqs_per_thread=%d, packed=%d%s",
+                gls ? "generalized " : "", l.prec, k, fpt, packed,
+                abl ? " (the trig/staging ablation kernels are FP32, scalar, k_reseed=freqs_per_thread=16)" : "");
+  l.abl = abl;
   l.k = k;
   l.fpt = fpt;
   l.threads = threads;
@@ -186,7 +193,7 @@ lsp_status resolve(int64_t n_obj, int64_t total_nt, const lsp_grid* g, const lsp
   l.off_part = take(split > 1 ? (size_t)split * l.n_f * 4 * (l.prec ? 8 : 4) : 0);
   l.total = off;
 
-  int bps = main_blocks_per_sm(l.prec, l.packed, l.k, l.fpt, l.threads, l.top, l.gls);
+  int bps = main_blocks_per_sm(l.prec, l.packed, l.k, l.fpt, l.threads, l.top, l.gls, l.abl);
   if (bps <= 0) {
     cudaGetLastError();
     bps = 1;
@@ -223,6 +230,7 @@ lsp_status run(const Layout& L, const double* t, const void* y, const int64_t* o
   MainLaunch ml;
   ml.prec = L.prec;
   ml.packed = L.packed;
+  ml.abl = L.abl;
   ml.k_reseed = L.k;
   ml.fpt = L.fpt;
   ml.gls = L.gls;
@@ -446,6 +454,8 @@ lsp_config config_of(const Layout& L) {
   c.block_threads = L.threads;
   c.obs_split = L.split;
   c.packed = L.packed;
+  c.trig = L.abl % 3;
+  c.staging = L.abl / 3;
   return c;
 }
 
@@ -539,6 +549,8 @@ bool cache_lookup(const char* path, const std::string& key, lsp_config* c) {
     if (get("k_reseed", &t.k_reseed) && get("freqs_per_thread", &t.freqs_per_thread) &&
         get("block_threads", &t.block_threads) && get("obs_split", &t.obs_split) &&
         get("packed", &t.packed)) {
+      get("trig", &t.trig);        // absent in older entries: 0
+      get("staging", &t.staging);
       *c = t;
       found = true;
     }
@@ -551,7 +563,8 @@ void cache_store(const char* path, const std::string& key, const lsp_config& c, 
   if (!f) return;
   f << "{\"key\": \"" << key << "\", \"k_reseed\": " << c.k_reseed << ", \"freqs_per_thread\": "
     << c.freqs_per_thread << ", \"block_threads\": " << c.block_threads << ", \"obs_split\": "
-    << c.obs_split << ", \"packed\": " << c.packed << ", \"ms\": " << ms << ", \"max_err\": " << err
+    << c.obs_split << ", \"packed\": " << c.packed << ", \"trig\": " << c.trig << ", \"staging\": "
+    << c.staging << ", \"ms\": " << ms << ", \"max_err\": " << err
     << "}\n";
 }
 
@@ -738,15 +751,25 @@ lsp_status lsp_plan_execute_host(lsp_plan* p, const double* t, const void* y,
 
 lsp_status lsp_plan_autotune(lsp_plan* p, const double* t, const void* y, const int64_t* offsets,
                              const char* cache_path, lsp_stream_t stream) {
+  return lsp_plan_autotune_ex(p, t, y, offsets, cache_path, 0, nullptr, 0, nullptr, stream);
+}
+
+lsp_status lsp_plan_autotune_ex(lsp_plan* p, const double* t, const void* y, const int64_t* offsets,
+                                const char* cache_path, int32_t flags, lsp_trial* trials,
+                                int32_t max_trials, int32_t* n_trials, lsp_stream_t stream) {
   g_err.clear();
+  if (n_trials) *n_trials = 0;
   if (!p) return fail(LSP_E_ARG, "plan is NULL");
+  if (flags & ~LSP_TUNE_ABLATIONS) return fail(LSP_E_ARG, "unknown autotune flags 0x%x", (unsigned)flags);
+  if (max_trials < 0 || (max_trials > 0 && !trials)) return fail(LSP_E_ARG, "trials must hold max_trials records");
+  const bool ablations = (flags & LSP_TUNE_ABLATIONS) != 0;
   lsp_status st = check_io(p->total_nt, t, y);
   if (st) return st;
   if (p->n_obj > 1 && !offsets) return fail(LSP_E_ARG, "offsets must not be NULL");
   cudaStream_t s = (cudaStream_t)stream;
   const std::string key = tune_key(p);
   lsp_config cached;
-  if (cache_path && cache_lookup(cache_path, key, &cached)) {
+  if (cache_path && !ablations && cache_lookup(cache_path, key, &cached)) {
     if (!apply_config(p, &cached)) return LSP_OK;
     g_err.clear();  // stale entry: tune again
   }
@@ -754,7 +777,7 @@ lsp_status lsp_plan_autotune(lsp_plan* p, const double* t, const void* y, const 
   // Candidates: reseed interval K, frequencies per thread, CTA size and (one
   // object) the N_t split.
   std::vector<lsp_config> cands;
-  auto add = [&](int k, int fpt, int thr, int packed, int split) {
+  auto add = [&](int k, int fpt, int thr, int packed, int split, int abl = 0) {
     lsp_config c;
     memset(&c, 0, sizeof c);
     c.k_reseed = k;
@@ -762,7 +785,9 @@ lsp_status lsp_plan_autotune(lsp_plan* p, const double* t, const void* y, const 
     c.block_threads = thr;
     c.packed = packed;
     c.obs_split = split;
-    if (main_variant_exists(p->opts.precision, packed, k, fpt)) cands.push_back(c);
+    c.trig = abl % 3;
+    c.staging = abl / 3;
+    if (main_variant_exists(p->opts.precision, packed, k, fpt, 0, abl)) cands.push_back(c);
   };
   std::vector<int> splits = {0};
   if (p->n_obj == 1) {
@@ -782,6 +807,9 @@ lsp_status lsp_plan_autotune(lsp_plan* p, const double* t, const void* y, const 
       for (int k : {4, 8, 16})
         for (int thr : {128, 256}) add(k, 2 * k, thr, 1, sp);
       for (int k : {8, 16}) add(k, k, 256, 0, sp);
+      if (ablations)
+        for (int abl = 1; abl <= 5; ++abl)
+          for (int thr : {128, 256}) add(16, 16, thr, 0, sp, abl);
     }
   }
 
@@ -844,6 +872,19 @@ lsp_status lsp_plan_autotune(lsp_plan* p, const double* t, const void* y, const 
   double best_err = 0.0;
   lsp_config best = p->cfg;
   bool any = false;
+  int32_t n_meas = 0;
+  auto record = [&](const lsp_config& c, float ms, double err, bool passed) {
+    if (n_meas < max_trials) {
+      lsp_trial& tr = trials[n_meas];
+      memset(&tr, 0, sizeof tr);
+      tr.config = c;
+      tr.ms = ms;
+      tr.max_err = (float)err;
+      tr.passed = passed ? 1 : 0;
+    }
+    ++n_meas;
+    if (n_trials) *n_trials = n_meas;
+  };
   for (const auto& c : cands) {
     Layout Lc;
     if (resolve(p->n_obj, p->total_nt, &p->grid, &p->opts, &c, &Lc)) { g_err.clear(); continue; }
@@ -861,7 +902,10 @@ lsp_status lsp_plan_autotune(lsp_plan* p, const double* t, const void* y, const 
       if (e == cudaSuccess) e = cudaMemcpyAsync(&err, d_err, sizeof(double), cudaMemcpyDeviceToHost, s);
       if (e == cudaSuccess) e = cudaStreamSynchronize(s);
       if (e != cudaSuccess) { cleanup(); return cuda_fail(e, "autotune gate"); }
-      if (!(err <= 1e-4)) continue;
+      if (!(err <= 1e-4)) {
+        record(c, -1.f, err, false);
+        continue;
+      }
     }
     if ((st = ensure_ws(p, Lc.total))) { cleanup(); return st; }
     Layout saved = p->L;
@@ -870,6 +914,7 @@ lsp_status lsp_plan_autotune(lsp_plan* p, const double* t, const void* y, const 
     st = time_runs(p, t, y, offsets, 3, s, &ms);
     p->L = saved;
     if (st) { cleanup(); return st; }
+    record(config_of(Lc), ms, err, true);
     if (ms < best_ms) {
       best_ms = ms;
       best = config_of(Lc);

@@ -44,6 +44,7 @@ struct MainLaunch {
   int k_reseed;  // chain length K
   int fpt;       // frequencies per thread (packed: 2K; scalar: K)
   int gls = 0;   // generalized periodogram kernels
+  int abl = 0;   // ablation kernel: trig + 3 * staging (lsp_config), 0 = production
   int threads;
   int grid;      // persistent CTAs
   int top;       // 1: top-k candidates
@@ -63,10 +64,11 @@ struct MainLaunch {
   const int32_t* win_start = nullptr;     // per-object window origins (packed FP32 kernels)
   int32_t win_len = 0;
 };
-bool main_variant_exists(int prec, int packed, int k_reseed, int fpt, int gls = 0);
+bool main_variant_exists(int prec, int packed, int k_reseed, int fpt, int gls = 0, int abl = 0);
 cudaError_t launch_main(const MainLaunch& ml, cudaStream_t stream);
 // CTAs of the main variant resident per SM (0 if the variant does not exist).
-int main_blocks_per_sm(int prec, int packed, int k_reseed, int fpt, int threads, int top, int gls = 0);
+int main_blocks_per_sm(int prec, int packed, int k_reseed, int fpt, int threads, int top, int gls = 0,
+                      int abl = 0);
 size_t main_dyn_smem(int prec, int fpt, int threads, int top);
 
 // Split-N_t combine (single object): sums the partial sums in a fixed order,

@@ -22,8 +22,21 @@ int occupancy(Kern kern, int threads, size_t dyn) {
   return nb;
 }
 
+// abl: ablation code trig + 3 * staging (0: the production kernels); the
+// ablation kernels are scalar, K = 16, standard periodogram only.
 template <typename Fn>
-bool dispatch_f32(int packed, int k, int gls, Fn&& fn) {
+bool dispatch_f32(int packed, int k, int gls, int abl, Fn&& fn) {
+  if (abl) {
+    if (packed || gls || k != 16) return false;
+    switch (abl) {
+      case 1: fn(main_scalar<float, RecF32, 16, 1, false>); return true;
+      case 2: fn(main_scalar<float, RecF32, 16, 2, false>); return true;
+      case 3: fn(main_scalar<float, RecF32, 16, 0, true>); return true;
+      case 4: fn(main_scalar<float, RecF32, 16, 1, true>); return true;
+      case 5: fn(main_scalar<float, RecF32, 16, 2, true>); return true;
+    }
+    return false;
+  }
   if (gls) {
     if (!packed) return false;
     switch (k) {
@@ -48,15 +61,15 @@ bool dispatch_f32(int packed, int k, int gls, Fn&& fn) {
 }
 }  // namespace
 
-bool main_variant_exists_f32(int packed, int k, int fpt, int gls) {
+bool main_variant_exists_f32(int packed, int k, int fpt, int gls, int abl) {
   if (fpt != (packed ? 2 * k : k)) return false;
-  return dispatch_f32(packed, k, gls, [](auto) {});
+  return dispatch_f32(packed, k, gls, abl, [](auto) {});
 }
 
-int main_blocks_per_sm_f32(int packed, int k, int fpt, int threads, int top, int gls) {
+int main_blocks_per_sm_f32(int packed, int k, int fpt, int threads, int top, int gls, int abl) {
   int nb = 0;
   size_t dyn = main_dyn_smem(0, fpt, threads, top);
-  dispatch_f32(packed, k, gls, [&](auto kern) { nb = occupancy(kern, threads, dyn); });
+  dispatch_f32(packed, k, gls, abl, [&](auto kern) { nb = occupancy(kern, threads, dyn); });
   return nb;
 }
 
@@ -78,7 +91,7 @@ cudaError_t launch_main_f32(const MainLaunch& ml, cudaStream_t stream) {
   p.win_start = ml.win_start;
   p.win_len = ml.win_len;
   cudaError_t err = cudaErrorInvalidValue;
-  dispatch_f32(ml.packed, ml.k_reseed, ml.gls, [&](auto kern) { err = launch_kernel(kern, ml, p, stream); });
+  dispatch_f32(ml.packed, ml.k_reseed, ml.gls, ml.abl, [&](auto kern) { err = launch_kernel(kern, ml, p, stream); });
   return err;
 }
 

@@ -562,14 +562,45 @@ __global__ void __launch_bounds__(256) main_f64_gls(MainParams<RecF64, double> p
   }
 }
 
+// (cos, sin) of a 32-bit fixed-point phase with CUDA's accurate FP32
+// sincospif: the argument (int)ph * 2^-31 half-cycles is exact up to the
+// integer-to-float rounding (<= 2^-25 half-cycle).
+__device__ __forceinline__ void sincos_accurate_f32(uint32_t ph, float& c, float& s) {
+  sincospif(__int2float_rn((int)ph) * 4.656612873077393e-10f, &s, &c);  // 2^-31
+}
+
+// One 32-byte record read straight from global memory (every thread of the
+// CTA reads the same record: an L1 broadcast).
+__device__ __forceinline__ RecF32 load_rec_global(const RecF32* rec) {
+  const uint4* q = reinterpret_cast<const uint4*>(rec);
+  const uint4 a = __ldg(q), b = __ldg(q + 1);
+  RecF32 r;
+  r.y = __uint_as_float(a.x);
+  r.cr = __uint_as_float(a.y);
+  r.sr = __uint_as_float(a.z);
+  r.a_hi = a.w;
+  r.b_hi = b.x;
+  r.b_lo = b.y;
+  r.a_lo = b.z;
+  r.pad = b.w;
+  return r;
+}
+
 // ------------------------------------------------------------------------
 // Scalar kernel: one reseed chain of K frequencies per thread.  Real = float
 // (FP32 records, SFU seeds) or double (FP64 records, FP64 sincospi seeds).
-template <typename Real, typename Rec, int K>
+//
+// Ablations (FP32 only; the paper's Section 3.6 / Table 3 and Section 4.12 /
+// Table 6 choices, selectable through lsp_config): TRIG = 1 evaluates every
+// pair's (cos, sin) with the SFU intrinsic from the exact phase, TRIG = 2
+// with the accurate sincospif, instead of the reseeded recurrence (TRIG = 0);
+// GLOBAL = true reads each observation record from global memory in every
+// thread instead of staging tiles in shared memory.
+template <typename Real, typename Rec, int K, int TRIG = 0, bool GLOBAL = false>
 __global__ void __launch_bounds__(256) main_scalar(MainParams<Rec, Real> p) {
   constexpr int F = K;
   constexpr int RW = sizeof(Rec) / 16;
-  __shared__ uint4 s_rec[RW * LSP_TILE_OBS];
+  __shared__ uint4 s_rec[GLOBAL ? 1 : RW * LSP_TILE_OBS];
   __shared__ double red_p[32];
   __shared__ int64_t red_k[32];
   __shared__ uint32_t s_item;
@@ -596,14 +627,8 @@ __global__ void __launch_bounds__(256) main_scalar(MainParams<Rec, Real> p) {
 #pragma unroll
     for (int m = 0; m < K; ++m) xc[m] = xs[m] = cc[m] = cs[m] = Real(0);
 
-    for (int64_t ts = ob; ts < oe; ts += LSP_TILE_OBS) {
-      const int nt = (int)((oe - ts) < LSP_TILE_OBS ? (oe - ts) : LSP_TILE_OBS);
-      const uint4* src = reinterpret_cast<const uint4*>(p.rec + ts);
-      for (int i = tid; i < RW * nt; i += blockDim.x) s_rec[i] = __ldg(src + i);
-      __syncthreads();
-      const int nt_c = (int64_t)k0 < p.n_f ? nt : 0;  // bins past the grid end: staging only
-      for (int j = 0; j < nt_c; ++j) {
-        const Rec r = srec[j];
+    auto one_obs = [&](const Rec& r) {
+      if constexpr (TRIG == 0) {
         Real c, s;
         if constexpr (std::is_same<Real, float>::value) {
           seed_sincos_f32(phase_hi32(r.a_hi, r.b_hi, r.b_lo, k0), c, s);
@@ -623,8 +648,36 @@ __global__ void __launch_bounds__(256) main_scalar(MainParams<Rec, Real> p) {
           cc[m] = fma(cm, cm, cc[m]);
           cs[m] = fma(cm, sm, cs[m]);
         });
+      } else {
+        const float y = r.y;
+#pragma unroll
+        for (int m = 0; m < K; ++m) {
+          const uint32_t ph = phase_hi32(r.a_hi, r.b_hi, r.b_lo, k0 + (uint32_t)m);
+          float c, s;
+          if constexpr (TRIG == 1)
+            seed_sincos_f32(ph, c, s);
+          else
+            sincos_accurate_f32(ph, c, s);
+          xc[m] = fmaf(y, c, xc[m]);
+          xs[m] = fmaf(y, s, xs[m]);
+          cc[m] = fmaf(c, c, cc[m]);
+          cs[m] = fmaf(c, s, cs[m]);
+        }
       }
-      __syncthreads();
+    };
+    if constexpr (GLOBAL) {
+      const int64_t oe_c = (int64_t)k0 < p.n_f ? oe : ob;  // bins past the grid end: nothing to do
+      for (int64_t j = ob; j < oe_c; ++j) one_obs(load_rec_global(p.rec + j));
+    } else {
+      for (int64_t ts = ob; ts < oe; ts += LSP_TILE_OBS) {
+        const int nt = (int)((oe - ts) < LSP_TILE_OBS ? (oe - ts) : LSP_TILE_OBS);
+        const uint4* src = reinterpret_cast<const uint4*>(p.rec + ts);
+        for (int i = tid; i < RW * nt; i += blockDim.x) s_rec[i] = __ldg(src + i);
+        __syncthreads();
+        const int nt_c = (int64_t)k0 < p.n_f ? nt : 0;  // bins past the grid end: staging only
+        for (int j = 0; j < nt_c; ++j) one_obs(srec[j]);
+        __syncthreads();
+      }
     }
 
     if (p.split == 1) {

@@ -7,9 +7,9 @@
 
 namespace lsp {
 
-bool main_variant_exists_f32(int packed, int k, int fpt, int gls);
+bool main_variant_exists_f32(int packed, int k, int fpt, int gls, int abl);
 bool main_variant_exists_f64(int k, int fpt, int gls);
-int main_blocks_per_sm_f32(int packed, int k, int fpt, int threads, int top, int gls);
+int main_blocks_per_sm_f32(int packed, int k, int fpt, int threads, int top, int gls, int abl);
 int main_blocks_per_sm_f64(int k, int fpt, int threads, int top, int gls);
 cudaError_t launch_main_f32(const MainLaunch& ml, cudaStream_t stream);
 cudaError_t launch_main_f64(const MainLaunch& ml, cudaStream_t stream);
@@ -18,15 +18,15 @@ size_t main_dyn_smem(int prec, int fpt, int threads, int top) {
   return top ? (size_t)threads * fpt * (prec ? sizeof(double) : sizeof(float)) : 0;
 }
 
-bool main_variant_exists(int prec, int packed, int k, int fpt, int gls) {
-  return prec ? (!packed && main_variant_exists_f64(k, fpt, gls))
-              : main_variant_exists_f32(packed, k, fpt, gls);
+bool main_variant_exists(int prec, int packed, int k, int fpt, int gls, int abl) {
+  return prec ? (!packed && !abl && main_variant_exists_f64(k, fpt, gls))
+              : main_variant_exists_f32(packed, k, fpt, gls, abl);
 }
 
-int main_blocks_per_sm(int prec, int packed, int k, int fpt, int threads, int top, int gls) {
-  if (!main_variant_exists(prec, packed, k, fpt, gls)) return 0;
+int main_blocks_per_sm(int prec, int packed, int k, int fpt, int threads, int top, int gls, int abl) {
+  if (!main_variant_exists(prec, packed, k, fpt, gls, abl)) return 0;
   return prec ? main_blocks_per_sm_f64(k, fpt, threads, top, gls)
-              : main_blocks_per_sm_f32(packed, k, fpt, threads, top, gls);
+              : main_blocks_per_sm_f32(packed, k, fpt, threads, top, gls, abl);
 }
 
 cudaError_t launch_main(const MainLaunch& ml, cudaStream_t stream) {

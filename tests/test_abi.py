@@ -176,3 +176,41 @@ def test_newer_entry_points_validate_without_launch(lsp_mod):
                                 None) == 1  # workspace too small
     # grid rule
     assert lsp_mod.grid_for_span(0.24, 12.0, 3650.0).n_f == round((12.0 - 0.24) / (0.1 / 3650.0))
+
+
+def test_struct_layouts_match_the_header(lsp_mod, tmp_path):
+    # the binding's ctypes structures against a C compiler's view of include/lsp.h
+    import subprocess
+    src = tmp_path / "layout.c"
+    src.write_text("""
+#include <stdio.h>
+#include <stddef.h>
+#include "lsp.h"
+#define F(T, m) printf(#T "." #m " %zu\\n", offsetof(T, m))
+int main(void) {
+  printf("lsp_grid %zu\\nlsp_opts %zu\\nlsp_peak %zu\\nlsp_config %zu\\nlsp_trial %zu\\nlsp_mlp_dims %zu\\n",
+         sizeof(lsp_grid), sizeof(lsp_opts), sizeof(lsp_peak), sizeof(lsp_config), sizeof(lsp_trial),
+         sizeof(lsp_mlp_dims));
+  F(lsp_config, packed); F(lsp_config, trig); F(lsp_config, staging);
+  F(lsp_trial, ms); F(lsp_trial, max_err); F(lsp_trial, passed);
+  F(lsp_peak, power); F(lsp_peak, freq); F(lsp_peak, period); F(lsp_peak, flags);
+  return 0;
+}
+""")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = dict(line.rsplit(" ", 1) for line in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                                check=True).stdout.split("\n") if line)
+    L = lsp_mod
+    assert int(out["lsp_grid"]) == ctypes.sizeof(L.Grid)
+    assert int(out["lsp_opts"]) == ctypes.sizeof(L.Opts)
+    assert int(out["lsp_config"]) == ctypes.sizeof(L.Config)
+    assert int(out["lsp_trial"]) == ctypes.sizeof(L.Trial)
+    assert int(out["lsp_mlp_dims"]) == ctypes.sizeof(L.MlpDims)
+    assert int(out["lsp_peak"]) == L.PEAK_DTYPE.itemsize
+    for name in ("packed", "trig", "staging"):
+        assert int(out["lsp_config." + name]) == getattr(L.Config, name).offset
+    for name in ("ms", "max_err", "passed"):
+        assert int(out["lsp_trial." + name]) == getattr(L.Trial, name).offset
+    for name in ("power", "freq", "period", "flags"):
+        assert int(out["lsp_peak." + name]) == L.PEAK_DTYPE.fields[name][1]

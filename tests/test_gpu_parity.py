@@ -493,3 +493,65 @@ def test_fma_rate_probe_is_plausible(env):
     assert 0.5 * f32_nominal < r["f32"] <= 1.02 * f32_nominal, r
     assert 0.5 * f32_nominal < r["f32x2"] <= 1.02 * f32_nominal, r
     assert 0.3 * n_sm * 2 * 2.07e9 < r["f64"] <= 1.02 * n_sm * 2 * 2.07e9, r
+
+
+# ------------------------------------------- ablations (Table 3, Table 6)
+ABLATIONS = [(trig, staging) for staging in (0, 1) for trig in (0, 1, 2) if trig or staging]
+
+
+@pytest.mark.parametrize("trig,staging", ABLATIONS, ids=lambda v: str(v))
+def test_ablation_kernels_match_oracle(env, small_batch, trig, staging):
+    # per-pair SFU / accurate sin-cos and global-memory observation reads:
+    # the same periodogram within the FP32 tolerance
+    lsp, torch, dev = env
+    b, ref = small_batch
+    g = lsp.Grid(b.grid.f_min, b.grid.f_max, b.grid.n_f)
+    t = _dev(torch, dev, b.t, torch.float64)
+    y = _dev(torch, dev, b.y, torch.float32)
+    off = _dev(torch, dev, b.offsets, torch.int64)
+    plan = lsp.Plan(b.n_obj, b.t.size, g)
+    plan.set_config(k_reseed=16, freqs_per_thread=16, block_threads=128, packed=0, obs_split=1,
+                    trig=trig, staging=staging)
+    assert plan.config["trig"] == trig and plan.config["staging"] == staging
+    power = torch.empty((b.n_obj, g.n_f), dtype=torch.float32, device=dev)
+    pk = lsp.peaks_to_numpy(plan.execute(t, y, off, power=power))
+    err = np.max(np.abs(power.cpu().numpy().astype(np.float64) - ref["fp32"]["power"]))
+    assert err <= TOL32, err
+    for o in range(b.n_obj):
+        assert_argmax_close(pk["idx"][o], ref["fp32"]["arg_idx"][o], ref["fp32"]["power"][o])
+    plan.close()
+
+
+def test_ablation_configs_are_checked(env, small_batch):
+    lsp, torch, dev = env
+    b, _ = small_batch
+    plan = lsp.Plan(b.n_obj, b.t.size, lsp.Grid(b.grid.f_min, b.grid.f_max, b.grid.n_f))
+    for bad in (dict(trig=3), dict(staging=2), dict(trig=1, packed=1, freqs_per_thread=32),
+                dict(trig=1, k_reseed=8, freqs_per_thread=8)):
+        cfg = dict(k_reseed=16, freqs_per_thread=16, block_threads=128, packed=0, obs_split=1, trig=0, staging=0)
+        cfg.update(bad)
+        with pytest.raises(lsp.LSPError):
+            plan.set_config(**cfg)
+    plan.close()
+
+
+def test_autotune_records_trials_including_ablations(env, small_batch, tmp_path):
+    lsp, torch, dev = env
+    b, ref = small_batch
+    g = lsp.Grid(b.grid.f_min, b.grid.f_max, b.grid.n_f)
+    t = _dev(torch, dev, b.t, torch.float64)
+    y = _dev(torch, dev, b.y, torch.float32)
+    off = _dev(torch, dev, b.offsets, torch.int64)
+    plan = lsp.Plan(b.n_obj, b.t.size, g)
+    cfg, trials = plan.autotune(t, y, off, cache_path=str(tmp_path / "t.jsonl"), ablations=True,
+                                return_trials=True)
+    seen = {(tr["config"]["trig"], tr["config"]["staging"]) for tr in trials}
+    assert set(ABLATIONS) <= seen
+    for tr in trials:
+        assert tr["passed"] and tr["ms"] > 0 and tr["max_err"] <= TOL32, tr
+    assert min(tr["ms"] for tr in trials) == pytest.approx(
+        min(tr["ms"] for tr in trials if tr["config"] == cfg), rel=1e-6)
+    pk = lsp.peaks_to_numpy(plan.execute(t, y, off))
+    for o in range(b.n_obj):
+        assert_argmax_close(pk["idx"][o], ref["fp32"]["arg_idx"][o], ref["fp32"]["power"][o])
+    plan.close()
