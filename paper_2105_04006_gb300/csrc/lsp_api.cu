@@ -71,7 +71,7 @@ struct Layout {
   int32_t n_chunks, n_res_chunks;
   int64_t n_items;
   int grid;  // persistent CTAs
-  size_t off_obj, off_rec, off_order, off_hist, off_queue, off_best, off_cand, off_part, total;
+  size_t off_obj, off_rec, off_order, off_hist, off_queue, off_best, off_cand, off_part, off_stats, total;
 };
 
 constexpr int64_t kMaxNf = (int64_t)1 << 31;  // k0 + F must fit in 32 bits
@@ -191,6 +191,7 @@ lsp_status resolve(int64_t n_obj, int64_t total_nt, const lsp_grid* g, const lsp
   l.off_best = take((size_t)n_obj * l.n_res_chunks * sizeof(ChunkBest));
   l.off_cand = take(l.top ? (size_t)n_obj * l.n_res_chunks * sizeof(ChunkCand) : 0);
   l.off_part = take(split > 1 ? (size_t)split * l.n_f * 4 * (l.prec ? 8 : 4) : 0);
+  l.off_stats = take(n_obj == 1 ? stats_slices_bytes(total_nt) : 0);
   l.total = off;
 
   int bps = main_blocks_per_sm(l.prec, l.packed, l.k, l.fpt, l.threads, l.top, l.gls, l.abl);
@@ -220,13 +221,15 @@ lsp_status run(const Layout& L, const double* t, const void* y, const int64_t* o
   void* part = L.split > 1 ? (void*)(ws + L.off_part) : nullptr;
   const bool y64 = L.prec == LSP_FP64;
 
+  // queue[0]: the main kernel's work counter; queue[1], queue[2]: last-CTA
+  // tickets of the one-object statistics and combine kernels
+  LSP_CUDA(cudaMemsetAsync(queue, 0, 16, st), "queue reset");
   LSP_CUDA(launch_stats(t, y, y64, offsets, L.n_obj, L.total_nt, L.center, L.norm, obj, st, L.gls != 0,
-                        dy),
+                        dy, L.n_obj == 1 ? ws + L.off_stats : nullptr, queue + 1),
            "prologue (statistics)");
   LSP_CUDA(launch_records(t, y, y64, obj, L.n_obj, L.total_nt, L.f_min, L.df, y64, rec, st, L.gls != 0, dy),
            "prologue (records)");
   if (order) LSP_CUDA(launch_lpt_order(obj, L.n_obj, hist, order, st), "work-queue order");
-  LSP_CUDA(cudaMemsetAsync(queue, 0, 16, st), "queue reset");
   MainLaunch ml;
   ml.prec = L.prec;
   ml.packed = L.packed;
@@ -253,10 +256,13 @@ lsp_status run(const Layout& L, const double* t, const void* y, const int64_t* o
   if (ev_main0) LSP_CUDA(cudaEventRecordWithFlags(ev_main0, st, cudaEventRecordExternal), "timing event");
   LSP_CUDA(launch_main(ml, st), "main kernel");
   if (ev_main1) LSP_CUDA(cudaEventRecordWithFlags(ev_main1, st, cudaEventRecordExternal), "timing event");
+  // one object, first maximum: the combine kernel writes the peak itself
+  const bool fused = L.split > 1 && !L.top && peaks;
   if (L.split > 1)
-    LSP_CUDA(launch_combine(L.prec, part, L.split, L.n_f, obj, rec, power_out, best, cand, st),
+    LSP_CUDA(launch_combine(L.prec, part, L.split, L.n_f, obj, rec, power_out, best, cand, st,
+                            fused ? peaks : nullptr, L.f_min, L.df, queue + 2),
              "split combine");
-  if (peaks)
+  if (peaks && !fused)
     LSP_CUDA(launch_finalize(obj, best, cand, L.n_obj, L.n_res_chunks, L.top_k, L.f_min, L.df,
                              peaks, st),
              "finalize");

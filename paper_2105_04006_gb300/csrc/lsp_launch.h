@@ -28,7 +28,12 @@ inline cudaError_t allow_dyn_smem(Kern kern, size_t dyn) {
 // NULL: unit weights).
 cudaError_t launch_stats(const double* t, const void* y, bool y64, const int64_t* offsets,
                          int64_t n_obj, int64_t total_nt, int center, int norm, ObjInfo* obj,
-                         cudaStream_t stream, bool gls = false, const void* dy = nullptr);
+                         cudaStream_t stream, bool gls = false, const void* dy = nullptr,
+                         void* slices_ws = nullptr, uint32_t* ticket = nullptr);
+// Scratch of the one-object statistics pass (slices_ws of launch_stats): with
+// it, and a zeroed ticket word, one object without offsets is reduced by
+// many CTAs; without it by one.
+size_t stats_slices_bytes(int64_t total_nt);
 cudaError_t launch_records(const double* t, const void* y, bool y64, const ObjInfo* obj,
                            int64_t n_obj, int64_t max_nt_single, double f_min, double df,
                            bool rec64, void* rec, cudaStream_t stream, bool gls = false,
@@ -72,12 +77,15 @@ int main_blocks_per_sm(int prec, int packed, int k_reseed, int fpt, int threads,
 size_t main_dyn_smem(int prec, int fpt, int threads, int top);
 
 // Split-N_t combine (single object): sums the partial sums in a fixed order,
-// evaluates the power, stores it (optional) and reduces chunk results.
+// evaluates the power, stores it (optional) and reduces chunk results; with
+// peaks, no candidates and a zeroed ticket word it also writes the first
+// maximum (no finalize launch needed).
 constexpr int kCombineThreads = 256;
 constexpr int kCombinePerThread = 4;
 cudaError_t launch_combine(int prec, const void* part, int split, int64_t n_f, const ObjInfo* obj,
                            const void* rec, void* power_out, ChunkBest* best, ChunkCand* cand,
-                           cudaStream_t stream);
+                           cudaStream_t stream, lsp_peak* peaks = nullptr, double f_min = 0.0,
+                           double df = 0.0, uint32_t* ticket = nullptr);
 
 // Per-object peaks from the chunk results.
 cudaError_t launch_finalize(const ObjInfo* obj, const ChunkBest* best, const ChunkCand* cand,

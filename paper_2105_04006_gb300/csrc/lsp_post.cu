@@ -35,14 +35,37 @@ cudaError_t launch_main(const MainLaunch& ml, cudaStream_t stream) {
 
 namespace {
 
+__device__ __forceinline__ lsp_peak make_peak(int64_t k, double p, double f_min, double df,
+                                              int flags) {
+  lsp_peak pk;
+  pk.flags = flags;
+  pk.reserved = 0;
+  if (flags || k < 0) {
+    pk.idx = -1;
+    pk.power = 0.0;
+    pk.freq = 0.0;
+    pk.period = 0.0;
+  } else {
+    pk.idx = k;
+    pk.power = p;
+    pk.freq = __dadd_rn(f_min, __dmul_rn((double)k, df));  // f_min + k df, two roundings
+    pk.period = 1.0 / pk.freq;
+  }
+  return pk;
+}
+
 // ------------------------------------------------------------- combine
 // Split-N_t single object: sum the S partial sums of each frequency in the
 // fixed order s = 0..S-1 (deterministic), then Eq. 2 and the chunk results.
+// With peaks (first maximum only), the last CTA to finish (ticket, zero on
+// entry) also reduces all chunk results in index order and writes the peak,
+// so no separate finalize launch follows.
 template <typename Real>
 __global__ void __launch_bounds__(kCombineThreads) combine_kernel(
     const Real* __restrict__ part, int split, int64_t n_f, const ObjInfo* __restrict__ obj,
     const RecF32* __restrict__ rec, Real* __restrict__ power_out, ChunkBest* __restrict__ best,
-    ChunkCand* __restrict__ cand) {
+    ChunkCand* __restrict__ cand, lsp_peak* __restrict__ peaks, double f_min, double df,
+    uint32_t* __restrict__ ticket) {
   constexpr int NP = kCombinePerThread;
   extern __shared__ __align__(16) unsigned char dyn_smem[];
   Real* s_pw = reinterpret_cast<Real*>(dyn_smem);
@@ -88,25 +111,27 @@ __global__ void __launch_bounds__(kCombineThreads) combine_kernel(
   else
     chunk_results<Real, NP>(pv, k0, kc0, n_f, best + blockIdx.x, cand ? cand + blockIdx.x : nullptr,
                             s_pw, red_p, red_k);
-}
-
-__device__ __forceinline__ lsp_peak make_peak(int64_t k, double p, double f_min, double df,
-                                              int flags) {
-  lsp_peak pk;
-  pk.flags = flags;
-  pk.reserved = 0;
-  if (flags || k < 0) {
-    pk.idx = -1;
-    pk.power = 0.0;
-    pk.freq = 0.0;
-    pk.period = 0.0;
-  } else {
-    pk.idx = k;
-    pk.power = p;
-    pk.freq = __dadd_rn(f_min, __dmul_rn((double)k, df));  // f_min + k df, two roundings
-    pk.period = 1.0 / pk.freq;
+  if (!peaks) return;
+  __shared__ bool s_last;
+  if (threadIdx.x == 0) {  // thread 0 wrote this CTA's chunk result
+    __threadfence();
+    s_last = atomicAdd(ticket, 1u) == gridDim.x - 1;
   }
-  return pk;
+  __syncthreads();
+  if (!s_last || threadIdx.x >= 32) return;
+  __threadfence();
+  double p = 0.0;
+  int64_t k = -1;
+  for (unsigned c = threadIdx.x; c < gridDim.x; c += 32) {
+    const double bp = __ldcg(&best[c].p);
+    const int64_t bk = __ldcg(&best[c].k);
+    if (better(bp, bk, p, k)) {
+      p = bp;
+      k = bk;
+    }
+  }
+  warp_best(p, k);
+  if (threadIdx.x == 0) peaks[0] = make_peak(k, p, f_min, df, oi.flags);
 }
 
 // First maximum per object: one warp per object, lanes stride the chunks.
@@ -308,16 +333,18 @@ cudaError_t launch_max_abs_diff(const float* a, const double* b, int64_t n, doub
 
 cudaError_t launch_combine(int prec, const void* part, int split, int64_t n_f, const ObjInfo* obj,
                            const void* rec, void* power_out, ChunkBest* best, ChunkCand* cand,
-                           cudaStream_t stream) {
+                           cudaStream_t stream, lsp_peak* peaks, double f_min, double df, uint32_t* ticket) {
   const int64_t per_cta = (int64_t)kCombineThreads * kCombinePerThread;
   const unsigned grid = (unsigned)((n_f + per_cta - 1) / per_cta);
   const size_t dyn = cand ? (size_t)per_cta * (prec ? 8 : 4) : 0;
+  if (cand || !ticket) peaks = nullptr;  // top-k peaks: the separate finalize
   if (prec)
     combine_kernel<double><<<grid, kCombineThreads, dyn, stream>>>(
-        (const double*)part, split, n_f, obj, nullptr, (double*)power_out, best, cand);
+        (const double*)part, split, n_f, obj, nullptr, (double*)power_out, best, cand, peaks, f_min, df, ticket);
   else
     combine_kernel<float><<<grid, kCombineThreads, dyn, stream>>>(
-        (const float*)part, split, n_f, obj, (const RecF32*)rec, (float*)power_out, best, cand);
+        (const float*)part, split, n_f, obj, (const RecF32*)rec, (float*)power_out, best, cand, peaks, f_min,
+        df, ticket);
   return cudaGetLastError();
 }
 

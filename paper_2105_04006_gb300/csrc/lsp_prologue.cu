@@ -68,13 +68,115 @@ __device__ double block_max(double v, double* sh) {
   return v;
 }
 
-// One CTA per object.  GLS: weighted statistics with w = 1/dy^2 (dy NULL:
-// unit weights) for the generalized periodogram.
+// Per-object statistics in one pass over the observations: with a shift K
+// (the object's first magnitude, so that the sums are about the mean's
+// order), sy = sum w (y - K), sw = sum w, s2 = sum w (y - K)^2, the time span
+// and a non-finite flag.  The centred sum of squares then follows exactly in
+// real arithmetic as s2 - 2 d sy + d^2 sw with d = mean - K; in FP64 the
+// shift keeps the cancellation to a few digits of the 16.  GLS: w = 1/dy^2
+// (dy NULL: unit weights) for the generalized periodogram.
+struct StatAcc {
+  double sy, sw, s2, tmin, tmax, bad;
+};
+constexpr int kStatSlice = 256;  // observations (and threads) per CTA of the one-object pass
+
+__device__ __forceinline__ StatAcc stat_identity() { return StatAcc{0.0, 0.0, 0.0, INFINITY, -INFINITY, 0.0}; }
+
+__device__ __forceinline__ void stat_merge(StatAcc& a, const StatAcc& b) {
+  a.sy += b.sy;
+  a.sw += b.sw;
+  a.s2 += b.s2;
+  a.tmin = fmin(a.tmin, b.tmin);
+  a.tmax = fmax(a.tmax, b.tmax);
+  a.bad += b.bad;
+}
+
+__device__ __forceinline__ void stat_warp_merge(StatAcc& a) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    StatAcc b;
+    b.sy = __shfl_xor_sync(0xffffffffu, a.sy, o);
+    b.sw = __shfl_xor_sync(0xffffffffu, a.sw, o);
+    b.s2 = __shfl_xor_sync(0xffffffffu, a.s2, o);
+    b.tmin = __shfl_xor_sync(0xffffffffu, a.tmin, o);
+    b.tmax = __shfl_xor_sync(0xffffffffu, a.tmax, o);
+    b.bad = __shfl_xor_sync(0xffffffffu, a.bad, o);
+    stat_merge(a, b);
+  }
+}
+
+// Block reduction of StatAcc; the result is valid in thread 0.  sh holds one
+// StatAcc per warp.
+__device__ __forceinline__ StatAcc stat_block_merge(StatAcc a, StatAcc* sh) {
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
+  stat_warp_merge(a);
+  if (l == 0) sh[w] = a;
+  __syncthreads();
+  if (w == 0) {
+    a = l < nw ? sh[l] : stat_identity();
+    stat_warp_merge(a);
+  }
+  __syncthreads();
+  return a;
+}
+
+template <typename YT, bool GLS>
+__device__ __forceinline__ void stat_accumulate(const double* __restrict__ t, const YT* __restrict__ y,
+                                                const YT* __restrict__ dy, int64_t b, int64_t e, double K,
+                                                StatAcc& a) {
+  for (int64_t j = b + threadIdx.x; j < e; j += blockDim.x) {
+    const double tj = t[j], yj = (double)y[j];
+    double wj = 1.0;
+    if (GLS && dy) {
+      const double ej = (double)dy[j];
+      if (!isfinite(ej) || !(ej > 0.0)) a.bad = 1.0;
+      wj = 1.0 / (ej * ej);
+    }
+    if (!isfinite(tj) || !isfinite(yj)) a.bad = 1.0;
+    const double d = yj - K;
+    a.sy = fma(wj, d, a.sy);
+    a.sw += wj;
+    a.s2 = fma(wj * d, d, a.s2);
+    a.tmin = fmin(a.tmin, tj);
+    a.tmax = fmax(a.tmax, tj);
+  }
+}
+
+template <bool GLS>
+__device__ __forceinline__ ObjInfo stat_finish(const StatAcc& a, double K, int64_t b, int64_t n, int flags,
+                                               int center) {
+  const double mean = ((GLS || center) && n > 0 && a.sw > 0.0) ? K + a.sy / a.sw : 0.0;
+  const double d = mean - K;
+  const double s2 = n > 0 ? a.s2 - 2.0 * d * a.sy + d * d * a.sw : 0.0;
+  if (a.bad > 0.0) flags |= LSP_FLAG_NONFINITE;
+  if (n < (GLS ? 3 : 2)) flags |= LSP_FLAG_FEW_OBS;
+  if (!(flags & LSP_FLAG_NONFINITE) && n > 0 && !(s2 > 0.0)) flags |= LSP_FLAG_ZERO_VAR;
+  ObjInfo oi;
+  oi.t0 = n > 0 ? 0.5 * (a.tmin + a.tmax) : 0.0;
+  oi.ymean = mean;
+  oi.sum_y2 = s2;
+  oi.begin = b;
+  oi.n = (int32_t)n;
+  oi.flags = flags;
+  oi.wsum = a.sw;
+  oi.wsum_f = (float)a.sw;
+  return oi;
+}
+
+__device__ __forceinline__ void stat_norm(ObjInfo& oi, int norm, bool gls) {
+  if (gls)  // the generalized power is normalised in the kernel; PSD form = P * sum_y2 / 2
+    oi.norm_scale = norm ? 1.0 : 0.5 * oi.sum_y2;
+  else
+    oi.norm_scale = (norm && oi.sum_y2 > 0.0) ? 2.0 / oi.sum_y2 : 1.0;
+  oi.norm_scale_f = (float)oi.norm_scale;
+}
+
+// Batches: one CTA per object.
 template <typename YT, bool GLS>
 __global__ void stats_kernel(const double* __restrict__ t, const YT* __restrict__ y,
                              const YT* __restrict__ dy, const int64_t* __restrict__ offsets,
                              int64_t total_nt, int center, int norm, ObjInfo* __restrict__ obj) {
-  __shared__ double sh[32];
+  __shared__ StatAcc sh[32];
   const int64_t o = blockIdx.x;
   int64_t b = 0, e = total_nt;
   int flags = 0;
@@ -87,57 +189,52 @@ __global__ void stats_kernel(const double* __restrict__ t, const YT* __restrict_
     }
   }
   const int64_t n = e - b;
-  double sy = 0.0, sw = 0.0, tmin = INFINITY, tmax = -INFINITY, bad = 0.0;
-  for (int64_t j = b + threadIdx.x; j < e; j += blockDim.x) {
-    double tj = t[j], yj = (double)y[j];
-    double wj = 1.0;
-    if (GLS && dy) {
-      const double ej = (double)dy[j];
-      if (!isfinite(ej) || !(ej > 0.0)) bad = 1.0;
-      wj = 1.0 / (ej * ej);
-    }
-    if (!isfinite(tj) || !isfinite(yj)) bad = 1.0;
-    sy += wj * yj;
-    sw += wj;
-    tmin = fmin(tmin, tj);
-    tmax = fmax(tmax, tj);
-  }
-  sy = block_sum(sy, sh);
-  sw = block_sum(sw, sh);
-  tmin = block_min(tmin, sh);
-  tmax = block_max(tmax, sh);
-  bad = block_sum(bad, sh);
-  const double mean = ((GLS || center) && n > 0 && sw > 0.0) ? sy / sw : 0.0;
-  double s2 = 0.0;
-  for (int64_t j = b + threadIdx.x; j < e; j += blockDim.x) {
-    double d = (double)y[j] - mean;
-    double wj = 1.0;
-    if (GLS && dy) {
-      const double ej = (double)dy[j];
-      wj = 1.0 / (ej * ej);
-    }
-    s2 += wj * d * d;
-  }
-  s2 = block_sum(s2, sh);
+  const double K = n > 0 ? (double)y[b] : 0.0;
+  StatAcc a = stat_identity();
+  stat_accumulate<YT, GLS>(t, y, dy, b, e, K, a);
+  a = stat_block_merge(a, sh);
   if (threadIdx.x == 0) {
-    if (bad > 0.0) flags |= LSP_FLAG_NONFINITE;
-    if (n < (GLS ? 3 : 2)) flags |= LSP_FLAG_FEW_OBS;
-    if (!(flags & LSP_FLAG_NONFINITE) && n > 0 && !(s2 > 0.0)) flags |= LSP_FLAG_ZERO_VAR;
-    ObjInfo oi;
-    oi.t0 = n > 0 ? 0.5 * (tmin + tmax) : 0.0;
-    oi.ymean = mean;
-    oi.sum_y2 = s2;
-    oi.begin = b;
-    oi.n = (int32_t)n;
-    oi.flags = flags;
-    if (GLS)  // the generalized power is normalised in the kernel; PSD form = P * sum_y2 / 2
-      oi.norm_scale = norm ? 1.0 : 0.5 * s2;
-    else
-      oi.norm_scale = (norm && s2 > 0.0) ? 2.0 / s2 : 1.0;
-    oi.norm_scale_f = (float)oi.norm_scale;
-    oi.wsum = sw;
-    oi.wsum_f = (float)sw;
+    ObjInfo oi = stat_finish<GLS>(a, K, b, n, flags, center);
+    stat_norm(oi, norm, GLS);
     obj[o] = oi;
+  }
+}
+
+// One object: CTAs reduce slices of `slice` observations into part[]; the
+// last CTA to finish (ticket, zero on entry) merges the partials in index
+// order, so the result does not depend on which CTA finished last.
+template <typename YT, bool GLS>
+__global__ void stats_slices_kernel(const double* __restrict__ t, const YT* __restrict__ y,
+                                    const YT* __restrict__ dy, int64_t n, int64_t slice, int center, int norm,
+                                    StatAcc* __restrict__ part, uint32_t* __restrict__ ticket,
+                                    ObjInfo* __restrict__ obj) {
+  __shared__ StatAcc sh[32];
+  __shared__ bool s_last;
+  const double K = n > 0 ? (double)y[0] : 0.0;
+  const int64_t b = (int64_t)blockIdx.x * slice;
+  const int64_t e = b + slice < n ? b + slice : n;
+  StatAcc a = stat_identity();
+  stat_accumulate<YT, GLS>(t, y, dy, b, e, K, a);
+  a = stat_block_merge(a, sh);
+  if (threadIdx.x == 0) {
+    part[blockIdx.x] = a;
+    __threadfence();
+    s_last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!s_last || threadIdx.x >= 32) return;
+  __threadfence();
+  StatAcc r = stat_identity();
+  for (unsigned s = threadIdx.x; s < gridDim.x; s += 32) {
+    const double* q = reinterpret_cast<const double*>(part + s);
+    StatAcc v{__ldcg(q), __ldcg(q + 1), __ldcg(q + 2), __ldcg(q + 3), __ldcg(q + 4), __ldcg(q + 5)};
+    stat_merge(r, v);
+  }
+  stat_warp_merge(r);
+  if (threadIdx.x == 0) {
+    ObjInfo oi = stat_finish<GLS>(r, K, 0, n, n > (int64_t)INT32_MAX ? LSP_FLAG_BAD_OFFSETS : 0, center);
+    stat_norm(oi, norm, GLS);
+    obj[0] = oi;
   }
 }
 
@@ -258,10 +355,31 @@ __global__ void scatter_kernel(const ObjInfo* __restrict__ obj, int64_t n_obj, u
 
 }  // namespace
 
+size_t stats_slices_bytes(int64_t total_nt) {
+  const int64_t slices = (total_nt + kStatSlice - 1) / kStatSlice;
+  return (size_t)(slices > 0 ? slices : 1) * sizeof(StatAcc);
+}
+
 cudaError_t launch_stats(const double* t, const void* y, bool y64, const int64_t* offsets,
                          int64_t n_obj, int64_t total_nt, int center, int norm, ObjInfo* obj,
-                         cudaStream_t stream, bool gls, const void* dy) {
+                         cudaStream_t stream, bool gls, const void* dy, void* slices_ws, uint32_t* ticket) {
   if (n_obj <= 0) return cudaSuccess;
+  if (n_obj == 1 && !offsets && slices_ws && ticket) {
+    // one object without offsets: spread the pass over CTAs of kStatSlice observations
+    int64_t g64 = (total_nt + kStatSlice - 1) / kStatSlice;
+    const unsigned g = (unsigned)(g64 > 0 ? g64 : 1);
+    StatAcc* part = (StatAcc*)slices_ws;
+#define LSP_STATS_SLICES(YT, G)                                                                              \
+  stats_slices_kernel<YT, G><<<g, kStatSlice, 0, stream>>>(t, (const YT*)y, (const YT*)dy, total_nt, kStatSlice, \
+                                                            center, norm, part, ticket, obj)
+    if (y64) {
+      if (gls) LSP_STATS_SLICES(double, true); else LSP_STATS_SLICES(double, false);
+    } else {
+      if (gls) LSP_STATS_SLICES(float, true); else LSP_STATS_SLICES(float, false);
+    }
+#undef LSP_STATS_SLICES
+    return cudaGetLastError();
+  }
   const int threads = n_obj == 1 ? 1024 : 128;
   const unsigned g = (unsigned)n_obj;
   if (y64) {
