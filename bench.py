@@ -344,6 +344,9 @@ def run_gpu(args, w, name):
     plan.execute_host(th, yh, oh, power=ph, peaks=pk_host)  # warm: allocates staging, captures
     barrier()
     e2e_ms = []
+    clk_e2e = ClockSampler(gpu_index)
+    clk_e2e.start()
+    clk_e2e.mark(0)
     for i in range(args.steps):
         flush.fill_(i & 0xFF)
         a, c = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -352,6 +355,8 @@ def run_gpu(args, w, name):
         c.record()
         c.synchronize()
         e2e_ms.append(a.elapsed_time(c))
+    clk_e2e.mark(1)
+    clocks_e2e = clk_e2e.stop()
     e2e_s = torch.tensor([sum(e2e_ms) / 1e3], dtype=torch.float64, device=dev)
     if dist is not None:
         dist.all_reduce(e2e_s, op=dist.ReduceOp.MAX)
@@ -402,7 +407,8 @@ def run_gpu(args, w, name):
                          "source_hash": src},
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": "objects/s", "h2d_bytes_per_step": int(h2d),
-                    "d2h_bytes_per_step": int(d2h), "ms_per_step": statistics.mean(e2e_ms)},
+                    "d2h_bytes_per_step": int(d2h), "ms_per_step": statistics.mean(e2e_ms),
+                    "ms_min": min(e2e_ms), "ms_max": max(e2e_ms), "clocks": clocks_e2e},
             "gpu_launches": plan.kernel_count * args.steps,
             "clocks": clocks,
         }
