@@ -44,6 +44,63 @@ def build(force: bool = False) -> str:
     return _LIB_PATH
 
 
+_SRC32 = os.path.join(_HERE, "lsp_cpu_fp32.c")
+_LIB32_PATH = os.path.join(_HERE, "_build", "liblsp_cpu_fp32.so")
+_lib32 = None
+
+
+def build_fp32(force: bool = False) -> str:
+    """Compile the FP32 CPU configuration (timing context, not an oracle)."""
+    os.makedirs(os.path.dirname(_LIB32_PATH), exist_ok=True)
+    stale = (not os.path.exists(_LIB32_PATH)) or os.path.getmtime(_LIB32_PATH) < os.path.getmtime(_SRC32)
+    if force or stale:
+        tmp = _LIB32_PATH + f".tmp{os.getpid()}"
+        subprocess.run(["gcc", "-O2", "-std=c11", "-fopenmp", "-fPIC", "-shared", _SRC32, "-o", tmp, "-lm"],
+                       check=True)
+        os.replace(tmp, _LIB32_PATH)
+    return _LIB32_PATH
+
+
+def _load32():
+    global _lib32
+    with _lock:
+        if _lib32 is None:
+            build_fp32()
+            lib = ctypes.CDLL(_LIB32_PATH)
+            P, d, i64 = ctypes.c_void_p, ctypes.c_double, ctypes.c_int64
+            lib.cpu32_lsp_batch_argmax.argtypes = [P, P, P, i64, d, d, i64, P, P]
+            lib.cpu32_lsp_batch_argmax.restype = ctypes.c_int
+            lib.cpu32_lsp_single.argtypes = [P, P, i64, d, d, i64, P, i64, P]
+            lib.cpu32_lsp_single.restype = ctypes.c_int
+            _lib32 = lib
+    return _lib32
+
+
+def fp32_batch_argmax(t, y, offsets, f_min, f_max, n_f):
+    """The paper's FP32 CPU configuration (two-scan Eq. 1-2 in single precision),
+    batch mode: first maximum of P_n per object.  Timing context only."""
+    t, y = _f64(t), _f64(y)
+    off = np.ascontiguousarray(offsets, dtype=np.int64)
+    n_obj = off.size - 1
+    idx = np.empty(n_obj, dtype=np.int64)
+    pw = np.empty(n_obj, dtype=np.float32)
+    if _load32().cpu32_lsp_batch_argmax(_ptr(t), _ptr(y), _ptr(off), n_obj, float(f_min), float(f_max),
+                                        int(n_f), _ptr(idx), _ptr(pw)):
+        raise MemoryError("cpu32_lsp_batch_argmax")
+    return idx, pw
+
+
+def fp32_single(t, y, f_min, f_max, n_f, k_sel):
+    """FP32 CPU configuration, one object, P_n at the indices ``k_sel``."""
+    t, y = _f64(t), _f64(y)
+    ks = np.ascontiguousarray(k_sel, dtype=np.int64)
+    out = np.empty(ks.size, dtype=np.float32)
+    if _load32().cpu32_lsp_single(_ptr(t), _ptr(y), t.size, float(f_min), float(f_max), int(n_f), _ptr(ks),
+                                  ks.size, _ptr(out)):
+        raise MemoryError("cpu32_lsp_single")
+    return out
+
+
 def _load():
     global _lib
     with _lock:

@@ -273,3 +273,20 @@ def test_gls_invariances_and_flags(oracle_mod):
     ee = np.array([1.0, 1.0, 1.0, 1.0, 1.0, 1.0, -1.0, 1.0])
     fl = oracle_mod.gls_batch(tt, yy, ee, off, 0.2, 6.0, 10)["flags"]
     assert fl[0] & oracle_mod.FLAG_FEW_OBS and fl[1] & oracle_mod.FLAG_ZERO_VAR and fl[2] & oracle_mod.FLAG_NONFINITE
+
+
+def test_fp32_cpu_configuration_tracks_the_oracle(oracle_mod):
+    oracle = oracle_mod
+    # the FP32 CPU configuration timed beside the oracle computes the same
+    # periodogram to FP32 accuracy (it is timing context, not a reference)
+    b = synth.ragged_survey(6, seed=77, grid=synth.Grid(0.24, 12.0, 3001))
+    ref = oracle.lsp_batch(b.t, b.y, b.offsets, 0.24, 12.0, 3001, return_power=True)
+    idx, pw = oracle.fp32_batch_argmax(b.t, b.y, b.offsets, 0.24, 12.0, 3001)
+    for o in range(b.n_obj):
+        assert abs(float(pw[o]) - ref["arg_pow"][o]) < 5e-3
+        assert ref["power"][o][idx[o]] >= ref["arg_pow"][o] - 5e-3
+    s = synth.single_small(n_t=300, grid=synth.Grid(0.1, 10.0, 2000))
+    ks = np.arange(0, 2000, 7)
+    p32 = oracle.fp32_single(s.t, s.y, 0.1, 10.0, 2000, ks)
+    p64 = oracle.lsp_single(s.t, s.y, 0.1, 10.0, 2000, k_sel=ks)[0]
+    assert np.max(np.abs(p32 - p64)) < 5e-3
