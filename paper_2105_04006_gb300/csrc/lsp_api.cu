@@ -812,7 +812,7 @@ lsp_status lsp_plan_autotune_ex(lsp_plan* p, const double* t, const void* y, con
     } else {
       // 64-thread CTAs: the same warps per SM at K = 16 with half the chunk,
       // so a ragged last chunk wastes less (measured: 1-2 % on N_f = 5e4)
-      for (int k : {4, 8, 16})
+      for (int k : {4, 8, 12, 16})
         for (int thr : {64, 128, 256}) add(k, 2 * k, thr, 1, sp);
       for (int k : {8, 16}) add(k, k, 256, 0, sp);
       if (ablations)

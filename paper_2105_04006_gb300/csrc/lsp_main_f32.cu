@@ -49,6 +49,7 @@ bool dispatch_f32(int packed, int k, int gls, int abl, Fn&& fn) {
     switch (k) {
       case 4: fn(main_f32_packed<4>); return true;
       case 8: fn(main_f32_packed<8>); return true;
+      case 12: fn(main_f32_packed<12>); return true;
       case 16: fn(main_f32_packed<16>); return true;
     }
   } else {

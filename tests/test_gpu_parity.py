@@ -88,6 +88,7 @@ FP32_VARIANTS = [
     dict(k_reseed=4, freqs_per_thread=8, block_threads=256),
     dict(k_reseed=8, freqs_per_thread=16, block_threads=256),
     dict(k_reseed=16, freqs_per_thread=32, block_threads=256),
+    dict(k_reseed=12, freqs_per_thread=24, block_threads=64),
     dict(k_reseed=8, freqs_per_thread=16, block_threads=128),
     dict(k_reseed=4, freqs_per_thread=8, block_threads=64),
     dict(k_reseed=8, freqs_per_thread=8, block_threads=256),
@@ -374,7 +375,7 @@ def test_autotune_keeps_parity(env, small_batch, tmp_path):
     plan = lsp.Plan(b.n_obj, b.t.size, g)
     cache = str(tmp_path / "tune.jsonl")
     cfg = plan.autotune(t, y, off, cache_path=cache)
-    assert cfg["k_reseed"] in (4, 8, 16)
+    assert cfg["k_reseed"] in (4, 8, 12, 16)
     pk = lsp.peaks_to_numpy(plan.execute(t, y, off))
     for o in range(b.n_obj):
         assert_argmax_close(pk["idx"][o], ref["fp32"]["arg_idx"][o], ref["fp32"]["power"][o])
