@@ -92,9 +92,9 @@ __device__ __forceinline__ Item decode_item(const P& p, int64_t item) {
 // FP32, two reseed chains of K frequencies per thread in packed f32x2 lanes:
 // lane 0 covers k0 .. k0+K-1, lane 1 covers k0+K .. k0+2K-1.
 //
-// The shared-memory tile holds the 32-byte records as they are.  Each
-// observation costs every thread two SFU seeds (one per chain), one packed
-// rotation and K-2 packed three-term steps (chain3).  (Measured alternatives
+// Each tile of observations is staged as expanded 64-byte entries (ObsF2
+// below).  Each observation costs every thread two SFU seeds (one per
+// chain), one packed rotation and K-2 packed three-term steps (chain3).  (Measured alternatives
 // that did not pay on GB300: issuing the next observation's seeds one step
 // ahead, integer bit-building of the seed angle instead of I2F, deriving the
 // second chain's seed from the first by a K-step rotation, unrolling the
@@ -111,7 +111,8 @@ __device__ __forceinline__ f2_t f2_of(uint32_t lo, uint32_t hi) {
 // and double.  neg_ flips the sign bit; dbl_ doubles by adding one to the
 // exponent field (exact for normal numbers; a zero or subnormal input, which
 // a rounded cos or sin of a grid step essentially never is, becomes a number
-// of magnitude <= 2^-125 instead, a negligible coefficient error).
+// of magnitude <= 2^-125 (FP32) or 2^-1021 (FP64) instead, a negligible
+// coefficient error).
 __device__ __forceinline__ f2_t mul_(f2_t a, f2_t b) { return f2_mul(a, b); }
 __device__ __forceinline__ f2_t fma_(f2_t a, f2_t b, f2_t c) { return f2_fma(a, b, c); }
 __device__ __forceinline__ f2_t neg_(f2_t a) { return a ^ 0x8000000080000000ull; }

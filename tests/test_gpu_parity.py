@@ -556,3 +556,23 @@ def test_autotune_records_trials_including_ablations(env, small_batch, tmp_path)
     for o in range(b.n_obj):
         assert_argmax_close(pk["idx"][o], ref["fp32"]["arg_idx"][o], ref["fp32"]["power"][o])
     plan.close()
+
+
+def test_autotune_ex_rejects_bad_arguments(env, small_batch):
+    import ctypes
+    lsp, torch, dev = env
+    b, _ = small_batch
+    g = lsp.Grid(b.grid.f_min, b.grid.f_max, b.grid.n_f)
+    t = _dev(torch, dev, b.t, torch.float64)
+    y = _dev(torch, dev, b.y, torch.float32)
+    off = _dev(torch, dev, b.offsets, torch.int64)
+    plan = lsp.Plan(b.n_obj, b.t.size, g)
+    P = ctypes.c_void_p
+    n = ctypes.c_int32(-1)
+    st = lsp.lib().lsp_plan_autotune_ex(plan._h, P(t.data_ptr()), P(y.data_ptr()), P(off.data_ptr()), None, 2,
+                                        None, 0, ctypes.byref(n), None)
+    assert st == 1 and n.value == 0  # LSP_E_ARG: unknown flag
+    st = lsp.lib().lsp_plan_autotune_ex(plan._h, P(t.data_ptr()), P(y.data_ptr()), P(off.data_ptr()), None, 0,
+                                        None, 4, None, None)
+    assert st == 1  # trials NULL with max_trials > 0
+    plan.close()
