@@ -460,6 +460,9 @@ def run_learned(args):
     test = L.labelled_set(n_obj, dev, "learned_infer", 1000 + rank)
     b, g = test["batch"], test["grid"]
     plan = lsp.Plan(b.n_obj, b.t.size, g)
+    if not args.no_tune:  # the plain full grid at its fastest configuration
+        plan.autotune(test["t"], test["y"], test["off"],
+                      cache_path=os.path.join(ROOT, "paper_2105_04006_gb300", "_build", "tune_cache.jsonl"))
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
 
     def timed(fn):
@@ -493,7 +496,7 @@ def run_learned(args):
                                                    "8 windows of 2048, fallback < 0.3",
                    "trained_on": trained_on, "stop_power": prop.stop_power,
                    "l2": "flushed between steps (256 MiB write)"},
-        "plain": {"value": b.n_obj / (ms_plain / 1e3), "ms_per_step": ms_plain},
+        "plain": {"value": b.n_obj / (ms_plain / 1e3), "ms_per_step": ms_plain, "kernel_config": plan.config},
         "speedup_vs_plain": ms_plain / ms_learned,
         "recovery": ev["recovery"], "fallback_fraction": ev["fallback"],
         "mean_windows": ev["mean_windows"], "pair_fraction": ev["pair_fraction"],

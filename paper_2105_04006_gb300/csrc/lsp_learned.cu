@@ -768,8 +768,12 @@ struct RefineLayout {
   size_t off_obj, off_rec, off_state, off_best, off_full, off_win, off_list, off_cnt, total;
   int n_chunks;
 };
-constexpr int kRefineK = 8;          // reseed interval of the refine kernel
-constexpr int kRefineThreads = 128;  // 128 threads x 16 frequencies = 2048 bins per item
+// The refine kernel's configuration: 64 threads x 32 frequencies = 2048 bins
+// per item (K = 16 packed chains; the fastest shape measured on GB300 for
+// 2048-bin chunks).  lsp_batch with k_reseed 16, freqs_per_thread 32 and
+// block_threads 64 runs the same kernel on the same chunks.
+constexpr int kRefineK = 16;
+constexpr int kRefineThreads = 64;
 
 void refine_layout(int64_t n_obj, int64_t total_nt, int64_t n_f, RefineLayout* r) {
   size_t off = 0;

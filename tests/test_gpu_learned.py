@@ -108,7 +108,8 @@ def test_refine_all_fallback_equals_full_grid(env, labelled):
     n = s["batch"].n_obj
     cls = torch.zeros((n, 2), dtype=torch.int32, device=dev)
     peaks, info = L.refine(s["t"], s["y"], s["off"], s["grid"], cls, 2, 2.0, 2.0)  # nothing stops
-    _, full = lsp.batch(s["t"], s["y"], s["off"], s["grid"])
+    # the refine's own kernel configuration: the same sums, bit for bit
+    _, full = lsp.batch(s["t"], s["y"], s["off"], s["grid"], k_reseed=16, freqs_per_thread=32, block_threads=64)
     a, b = lsp.peaks_to_numpy(peaks), lsp.peaks_to_numpy(full)
     np.testing.assert_array_equal(a["idx"], b["idx"])
     np.testing.assert_array_equal(a["power"], b["power"])
