@@ -492,17 +492,21 @@ __device__ void chunk_results_f32(const float (&pv)[NP], uint32_t k0, int64_t k_
   const int chunk_len = blockDim.x * NP;
   const int64_t nvalid64 = n_f - k_chunk0;
   const int nvalid = nvalid64 < chunk_len ? (int)nvalid64 : chunk_len;
+  // bin i of the chunk at pw[i + i / NP]: one padding word per thread, so a
+  // warp's stores and neighbour reads fall in distinct banks (without it, a
+  // stride of NP = 32 floats puts all 32 lanes on one bank)
   const int base = threadIdx.x * NP;
+  const int pbase = threadIdx.x * (NP + 1);
 #pragma unroll
-  for (int m = 0; m < NP; ++m) pw[base + m] = pv[m];
+  for (int m = 0; m < NP; ++m) pw[pbase + m] = pv[m];
   __syncthreads();
   unsigned long long t0 = 0ull, t1 = 0ull, t2 = 0ull;  // this thread's top-3 interior maxima
 #pragma unroll
   for (int m = 0; m < NP; ++m) {
     const int i = base + m;
     if (i >= 1 && i <= nvalid - 2) {
-      const float v = pw[i];
-      if (v > pw[i - 1] && v >= pw[i + 1]) {
+      const float v = pw[pbase + m];
+      if (v > pw[(i - 1) + (i - 1) / NP] && v >= pw[(i + 1) + (i + 1) / NP]) {
         const unsigned long long key = pkey(v, (uint32_t)(k_chunk0 + i));
         if (key > t0) { t2 = t1; t1 = t0; t0 = key; }
         else if (key > t1) { t2 = t1; t1 = key; }
@@ -524,9 +528,9 @@ __device__ void chunk_results_f32(const float (&pv)[NP], uint32_t k0, int64_t k_
     out.nvalid = nvalid;
     out.pad = 0;
     out.first[0] = nvalid > 0 ? (double)pw[0] : 0.0;
-    out.first[1] = nvalid > 1 ? (double)pw[1] : 0.0;
-    out.last[0] = nvalid > 0 ? (double)pw[nvalid - 1] : 0.0;
-    out.last[1] = nvalid > 1 ? (double)pw[nvalid - 2] : 0.0;
+    out.first[1] = nvalid > 1 ? (double)pw[1 + 1 / NP] : 0.0;
+    out.last[0] = nvalid > 0 ? (double)pw[(nvalid - 1) + (nvalid - 1) / NP] : 0.0;
+    out.last[1] = nvalid > 1 ? (double)pw[(nvalid - 2) + (nvalid - 2) / NP] : 0.0;
     *cand_out = out;
   }
   __syncthreads();

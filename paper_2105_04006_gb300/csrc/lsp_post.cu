@@ -15,7 +15,8 @@ cudaError_t launch_main_f32(const MainLaunch& ml, cudaStream_t stream);
 cudaError_t launch_main_f64(const MainLaunch& ml, cudaStream_t stream);
 
 size_t main_dyn_smem(int prec, int fpt, int threads, int top) {
-  return top ? (size_t)threads * fpt * (prec ? sizeof(double) : sizeof(float)) : 0;
+  // FP32: one padding word per thread (chunk_results_f32)
+  return top ? (size_t)threads * (prec ? fpt * sizeof(double) : (fpt + 1) * sizeof(float)) : 0;
 }
 
 bool main_variant_exists(int prec, int packed, int k, int fpt, int gls, int abl) {
@@ -336,7 +337,9 @@ cudaError_t launch_combine(int prec, const void* part, int split, int64_t n_f, c
                            cudaStream_t stream, lsp_peak* peaks, double f_min, double df, uint32_t* ticket) {
   const int64_t per_cta = (int64_t)kCombineThreads * kCombinePerThread;
   const unsigned grid = (unsigned)((n_f + per_cta - 1) / per_cta);
-  const size_t dyn = cand ? (size_t)per_cta * (prec ? 8 : 4) : 0;
+  // chunk_results keeps the chunk's powers in shared memory (FP32: one
+  // padding word per thread)
+  const size_t dyn = cand ? (prec ? (size_t)per_cta * 8 : (size_t)kCombineThreads * (kCombinePerThread + 1) * 4) : 0;
   if (cand || !ticket) peaks = nullptr;  // top-k peaks: the separate finalize
   if (prec)
     combine_kernel<double><<<grid, kCombineThreads, dyn, stream>>>(
