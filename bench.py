@@ -154,6 +154,24 @@ def recorded_traffic(workload, src_hash):
 
 
 # ------------------------------------------------------------- CPU baseline
+def parity_vs_oracle(ref, peaks_np, top_k, power_np=None, precision="fp32"):
+    """This run's results against the oracle's on the CPU-baseline sample."""
+    tol = 1e-4 if precision == "fp32" else 1e-10
+    if ref is None:
+        return None
+    if ref["kind"] == "single":
+        if power_np is None:
+            return None
+        err = float(np.max(np.abs(power_np.reshape(-1)[ref["k"]].astype(np.float64) - ref["power"])))
+        return {"compared": f"P_n at {ref['k'].size} sampled frequencies", "max_abs_err": err,
+                "tolerance": tol, "within": err <= tol}
+    first = peaks_np.reshape(-1, top_k)[ref["objects"], 0]
+    dk = np.abs(first["idx"].astype(np.int64) - ref["arg_idx"].astype(np.int64))
+    err = float(np.max(np.abs(first["power"] - ref["arg_pow"])))
+    return {"compared": f"first maximum of {dk.size} sampled objects", "argmax_within_1_bin": float(np.mean(dk <= 1)),
+            "argmax_exact": float(np.mean(dk == 0)), "max_abs_err_peak_power": err, "tolerance": tol}
+
+
 def cpu_baseline(b, n_sample, top_k):
     import oracle
     oracle.build()
@@ -163,8 +181,10 @@ def cpu_baseline(b, n_sample, top_k):
         n_sel = int(min(g.n_f, max(1000, 4e9 // max(1, b.t.size))))
         ks = np.linspace(0, g.n_f - 1, n_sel).astype(np.int64)
         t0 = time.perf_counter()
-        oracle.lsp_single(b.t, b.y.astype(np.float32).astype(np.float64), g.f_min, g.f_max, g.n_f, k_sel=ks)
+        p_orc, _ = oracle.lsp_single(b.t, b.y.astype(np.float32).astype(np.float64), g.f_min, g.f_max, g.n_f,
+                                     k_sel=ks)
         dt = time.perf_counter() - t0
+        cpu_baseline.ref = {"kind": "single", "k": ks, "power": p_orc}
         frac = n_sel / g.n_f
         pairs = b.t.size * n_sel
         what = ("the whole object" if n_sel == g.n_f else
@@ -181,9 +201,10 @@ def cpu_baseline(b, n_sample, top_k):
     idx = np.linspace(0, b.n_obj - 1, n_sample).astype(np.int64)
     sub, what = b.subset(idx), f"{n_sample} objects evenly spaced over the batch"
     t0 = time.perf_counter()
-    oracle.lsp_batch(sub.t, sub.y.astype(np.float32).astype(np.float64), sub.offsets, g.f_min, g.f_max,
-                     g.n_f, top_k=top_k, return_power=False)
+    res = oracle.lsp_batch(sub.t, sub.y.astype(np.float32).astype(np.float64), sub.offsets, g.f_min, g.f_max,
+                           g.n_f, top_k=top_k, return_power=False)
     dt = time.perf_counter() - t0
+    cpu_baseline.ref = {"kind": "batch", "objects": idx, "arg_idx": res["arg_idx"], "arg_pow": res["arg_pow"]}
     t0 = time.perf_counter()
     oracle.fp32_batch_argmax(sub.t, sub.y.astype(np.float32).astype(np.float64), sub.offsets, g.f_min, g.f_max,
                              g.n_f)
@@ -396,6 +417,11 @@ def run_gpu(args, w, name):
     line = None
     if rank == 0:
         cpu = None if args.no_cpu else cpu_baseline(b, w["cpu_sample"], w["top_k"])
+        parity = None
+        if cpu is not None:  # this run's own results against the oracle on the same sample
+            pk_np = lsp.peaks_to_numpy(peaks)
+            pw_np = power.cpu().numpy() if power is not None else None
+            parity = parity_vs_oracle(getattr(cpu_baseline, "ref", None), pk_np, w["top_k"], pw_np, args.precision)
         line = {
             "impl": "gb300", "metric": METRIC, "value": value, "unit": "objects/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": statistics.mean(step_ms),
@@ -417,6 +443,7 @@ def run_gpu(args, w, name):
                          if (peak and not fp64) else achieved * KERNEL_OPS_PER_PAIR / OPS_PER_PAIR / ceiling,
                          "source_hash": src},
             "cpu_baseline": cpu,
+            "parity_vs_oracle": parity,
             "e2e": {"value": e2e_value, "unit": "objects/s", "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(d2h), "ms_per_step": statistics.mean(e2e_ms),
                     "ms_min": min(e2e_ms), "ms_max": max(e2e_ms), "clocks": clocks_e2e},

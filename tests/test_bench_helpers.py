@@ -1,0 +1,39 @@
+"""CPU checks of bench.py's host-side helpers (no GPU)."""
+import os
+import sys
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+
+def _peaks(idx, power):
+    dt = np.dtype([("idx", "<i8"), ("power", "<f8"), ("freq", "<f8"), ("period", "<f8"), ("flags", "<i4"),
+                   ("reserved", "<i4")])
+    a = np.zeros(len(idx), dtype=dt)
+    a["idx"] = idx
+    a["power"] = power
+    return a
+
+
+def test_parity_vs_oracle_batch_top1_and_top3():
+    import bench
+    ref = {"kind": "batch", "objects": np.array([0, 2]), "arg_idx": np.array([10, 20]),
+           "arg_pow": np.array([0.5, 0.25])}
+    got = bench.parity_vs_oracle(ref, _peaks([10, 99, 22], [0.50001, 0.1, 0.25]), 1)
+    assert got["argmax_within_1_bin"] == 0.5 and got["argmax_exact"] == 0.5
+    assert abs(got["max_abs_err_peak_power"] - 1e-5) < 1e-12
+    # top-3 rows: only each object's first entry is its maximum
+    pk = _peaks([10, 3, 4, 0, 0, 0, 21, 5, 6], [0.5, 0.4, 0.3, 0, 0, 0, 0.25, 0.2, 0.1])
+    got = bench.parity_vs_oracle(ref, pk, 3)
+    assert got["argmax_within_1_bin"] == 1.0 and got["argmax_exact"] == 0.5
+
+
+def test_parity_vs_oracle_single_object():
+    import bench
+    ref = {"kind": "single", "k": np.array([1, 3]), "power": np.array([0.2, 0.4])}
+    power = np.array([0.0, 0.2 + 3e-5, 0.0, 0.4], dtype=np.float32)
+    got = bench.parity_vs_oracle(ref, None, 1, power)
+    assert got["within"] and abs(got["max_abs_err"] - 3e-5) < 1e-6
+    assert bench.parity_vs_oracle(None, None, 1) is None
