@@ -399,6 +399,67 @@ def run_gls(args, w, name):
     return 0
 
 
+def run_periodogram_return(args, w, name):
+    """Section 3.5's transfer step on GB300: the full periodogram of a workload
+    returned to the host by each route the library offers, device time per step
+    (CUDA events on the launching stream, median of the steps)."""
+    import torch
+    import paper_2105_04006_gb300 as lsp
+
+    rank, world, local = dist_env()
+    if world > 1:
+        raise SystemExit("--periodogram-return runs on one GPU")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    b = make_workload(name, rank, args.n_obj)
+    g = lsp.Grid(b.grid.f_min, b.grid.f_max, b.grid.n_f)
+    t = torch.tensor(b.t, dtype=torch.float64, device=dev)
+    y = torch.tensor(b.y.astype(np.float32), device=dev)
+    off = torch.tensor(b.offsets, dtype=torch.int64, device=dev) if b.n_obj > 1 else None
+    plan = lsp.Plan(b.n_obj, b.t.size, g)
+    if not args.no_tune:
+        plan.autotune(t, y, off, cache_path=os.path.join(ROOT, "paper_2105_04006_gb300", "_build", "tune_cache.jsonl"))
+    shape = (b.n_obj, g.n_f)
+    p_dev = torch.empty(shape, dtype=torch.float32, device=dev)
+    p_pin = torch.empty(shape, dtype=torch.float32).pin_memory()
+    p_pag = torch.from_numpy(np.empty(shape, dtype=np.float32))
+    peaks = plan.peaks_buffer(dev)
+    routes = {
+        "peaks only (no periodogram)": lambda: plan.execute(t, y, off, peaks=peaks),
+        "periodogram into HBM": lambda: plan.execute(t, y, off, power=p_dev, peaks=peaks),
+        "into HBM, then copy to pinned host memory":
+            lambda: (plan.execute(t, y, off, power=p_dev, peaks=peaks), p_pin.copy_(p_dev, non_blocking=True)),
+        "into HBM, then copy to pageable host memory":
+            lambda: (plan.execute(t, y, off, power=p_dev, peaks=peaks), p_pag.copy_(p_dev)),
+        "written by the kernels straight into pinned host memory":
+            lambda: plan.execute(t, y, off, power=p_pin, peaks=peaks),
+    }
+    out = {}
+    for label, fn in routes.items():
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        ms = []
+        for _ in range(args.steps):
+            a, c = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            fn()
+            c.record()
+            c.synchronize()
+            ms.append(a.elapsed_time(c))
+        out[label] = statistics.median(ms)
+    nbytes = b.n_obj * g.n_f * 4
+    same = bool(torch.equal(p_pin, p_dev.cpu()))
+    plan.close()
+    copy_ms = out["into HBM, then copy to pinned host memory"] - out["periodogram into HBM"]
+    print(json.dumps({"impl": "gb300", "mode": "periodogram_return", "workload": name, "n_obj": b.n_obj,
+                      "n_f": g.n_f, "periodogram_bytes": nbytes, "ms_per_step": out,
+                      "copy_GB_per_s": nbytes / (copy_ms * 1e-3) / 1e9 if copy_ms > 0 else None,
+                      "pinned_direct_equals_device": same,
+                      "timing": "device time per step, CUDA events, median; L2 not flushed"}), flush=True)
+    return 0
+
+
 def run_ablations(args, lsp, torch, plan, b, t, y, off, name, rank):
     """The paper's kernel comparisons on GB300 through the autotuner: every candidate
     configuration, including the ablation kernels (per-pair SFU or accurate sin/cos
@@ -681,6 +742,8 @@ def main():
     ap.add_argument("--config", default=None,
                     help="force a kernel configuration: k_reseed,freqs_per_thread,block_threads,obs_split,packed"
                          "[,trig,staging]")
+    ap.add_argument("--periodogram-return", action="store_true",
+                    help="time the routes that return a full periodogram to the host (Section 3.5)")
     ap.add_argument("--gls", action="store_true",
                     help="the generalized periodogram (photometric errors, floating mean) on a batch workload")
     ap.add_argument("--ablations", action="store_true",
@@ -701,6 +764,8 @@ def main():
         return run_reference(args, w, args.workload)
     if args.gls:
         return run_gls(args, w, args.workload)
+    if args.periodogram_return:
+        return run_periodogram_return(args, w, args.workload)
     return run_gpu(args, w, args.workload)
 
 
