@@ -23,7 +23,7 @@ inline cudaError_t allow_dyn_smem(Kern kern, size_t dyn) {
 }
 
 // Prologue, Section 2 (zero-mean magnitudes) and the per-observation phase
-// data of the rotation recurrence.  y is float (y64 = false) or double.
+// data of the grid recurrences (rotation step, three-term coefficients).  y is float (y64 = false) or double.
 // gls: weighted statistics / records of the generalized periodogram (dy
 // NULL: unit weights).
 cudaError_t launch_stats(const double* t, const void* y, bool y64, const int64_t* offsets,

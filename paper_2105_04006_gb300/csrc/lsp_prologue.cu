@@ -2,8 +2,9 @@
 //
 // Section 2 assumes zero-mean magnitudes; the paper excludes this step from
 // its timings (Section 4.1).  Here it runs on the GPU in FP64:
-//   stats:   mean of y, sum of centred y^2, time span (t0 = midpoint), flags;
-//   records: y - mean, and the phase data of the rotation recurrence:
+//   stats:   mean of y, sum of centred y^2, time span (t0 = midpoint), flags
+//            (one pass of shifted sums);
+//   records: y - mean, and the phase data of the grid recurrences:
 //            a = frac(f_min (t - t0)), b = frac(df (t - t0)) as 64-bit fixed
 //            point (2^64 = one cycle), and (cos, sin)(2 pi b).
 // Subtracting t0 keeps |t - t0| <= half the span, so the FP64 products carry
