@@ -299,7 +299,10 @@ def run_gls(args, w, name):
     y = torch.tensor(yv, device=dev)
     e = torch.tensor(dy, device=dev)
     off = torch.tensor(b.offsets, dtype=torch.int64, device=dev)
-    opts = lsp.make_opts(precision=args.precision, top_k=w["top_k"])
+    kw = {}
+    if args.config:  # k_reseed,freqs_per_thread,block_threads for the generalized kernels
+        kw = dict(zip(("k_reseed", "freqs_per_thread", "block_threads"), (int(v) for v in args.config.split(",")[:3])))
+    opts = lsp.make_opts(precision=args.precision, top_k=w["top_k"], **kw)
     ws = torch.empty(max(lsp.workspace_size_gls(b.n_obj, b.t.size, g, opts), 256), dtype=torch.uint8, device=dev)
     peaks = torch.empty(b.n_obj * w["top_k"] * 40, dtype=torch.uint8, device=dev)
     L = lsp.lib()
@@ -387,7 +390,7 @@ def run_gls(args, w, name):
         "data": "synthetic",
         "config": {"workload": name + "+gls", "shape": w["desc"] + ", dy ~ U[0.02, 0.3]", "n_obj": b.n_obj,
                    "total_nt": int(b.t.size), "n_f": g.n_f, "l2": "flushed between steps (256 MiB write)",
-                   "kernel": "main_f32_packed_gls" if not fp64 else "main_f64_gls"},
+                   "kernel": "main_f32_packed_gls" if not fp64 else "main_f64_gls", "options": kw},
         "pairs_per_s": achieved * 1e9,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gpair/s",
                      "frac": achieved / peak if peak else None, "traffic": None,
