@@ -320,7 +320,8 @@ lsp_status lsp_plan_autotune_ex(lsp_plan* plan, const double* t, const void* y, 
  */
 lsp_status lsp_plan_enable_timing(lsp_plan* plan, int32_t enable);
 lsp_status lsp_plan_main_kernel_ms(lsp_plan* plan, float* ms);
-/* Number of the library's kernels one execution of the plan launches. */
+/* Number of the library's kernels one execution of the plan launches when
+ * peaks are requested (a memset, not a kernel, clears the work counters). */
 lsp_status lsp_plan_kernel_count(const lsp_plan* plan, int32_t* count);
 
 lsp_status lsp_plan_get_config(const lsp_plan* plan, lsp_config* config);

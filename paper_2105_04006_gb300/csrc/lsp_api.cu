@@ -649,8 +649,11 @@ lsp_status lsp_plan_main_kernel_ms(lsp_plan* p, float* ms) {
 lsp_status lsp_plan_kernel_count(const lsp_plan* p, int32_t* count) {
   if (!p || !count) return fail(LSP_E_ARG, "NULL argument");
   const Layout& L = p->L;
-  // statistics + records + main (+ 3 for the LPT order) (+ combine) (+ finalize)
-  *count = 3 + (L.n_obj > 1 ? 3 : 0) + (L.split > 1 ? 1 : 0) + 1;
+  // statistics + records + main (+ 3 for the LPT order) (+ combine) (+ finalize,
+  // which a split single object with a first-maximum output folds into the
+  // combine); peaks requested
+  const bool fused = L.split > 1 && !L.top;
+  *count = 3 + (L.n_obj > 1 ? 3 : 0) + (L.split > 1 ? 1 : 0) + (fused ? 0 : 1);
   return LSP_OK;
 }
 
