@@ -576,3 +576,4 @@ def test_autotune_ex_rejects_bad_arguments(env, small_batch):
                                         None, 4, None, None)
     assert st == 1  # trials NULL with max_trials > 0
     plan.close()
+
