@@ -427,6 +427,17 @@ def run_periodogram_return(args, w, name):
     p_pin = torch.empty(shape, dtype=torch.float32).pin_memory()
     p_pag = torch.from_numpy(np.empty(shape, dtype=np.float32))
     peaks = plan.peaks_buffer(dev)
+    t_h = torch.from_numpy(np.ascontiguousarray(b.t)).pin_memory()
+    y_h = torch.from_numpy(b.y.astype(np.float32)).pin_memory()
+    off_h = torch.from_numpy(np.ascontiguousarray(b.offsets)).pin_memory() if off is not None else None
+    pk_h = np.empty(b.n_obj, dtype=lsp.PEAK_DTYPE)
+
+    def host(parts, out):
+        def fn():
+            plan.set_host_parts(parts)
+            plan.execute_host(t_h, y_h, off_h, power=out, peaks=pk_h)
+        return fn
+
     routes = {
         "peaks only (no periodogram)": lambda: plan.execute(t, y, off, peaks=peaks),
         "periodogram into HBM": lambda: plan.execute(t, y, off, power=p_dev, peaks=peaks),
@@ -436,7 +447,11 @@ def run_periodogram_return(args, w, name):
             lambda: (plan.execute(t, y, off, power=p_dev, peaks=peaks), p_pag.copy_(p_dev)),
         "written by the kernels straight into pinned host memory":
             lambda: plan.execute(t, y, off, power=p_pin, peaks=peaks),
+        "host entry point (inputs in, peaks out), one pass into pinned memory": host(1, p_pin),
     }
+    for n in (2, 4, 8, 16):
+        routes[f"host entry point, {n} object groups, copies overlapped, pinned"] = host(n, p_pin)
+    routes["host entry point, 8 object groups, copies overlapped, pageable"] = host(8, p_pag)
     out = {}
     for label, fn in routes.items():
         for _ in range(args.warmup):
@@ -452,13 +467,15 @@ def run_periodogram_return(args, w, name):
             ms.append(a.elapsed_time(c))
         out[label] = statistics.median(ms)
     nbytes = b.n_obj * g.n_f * 4
-    same = bool(torch.equal(p_pin, p_dev.cpu()))
+    same = bool(torch.equal(p_pin, p_dev.cpu())) and bool(torch.equal(p_pag, p_dev.cpu()))
+    plan.set_host_parts(0)
+    default_parts = plan.host_parts()
     plan.close()
     copy_ms = out["into HBM, then copy to pinned host memory"] - out["periodogram into HBM"]
     print(json.dumps({"impl": "gb300", "mode": "periodogram_return", "workload": name, "n_obj": b.n_obj,
                       "n_f": g.n_f, "periodogram_bytes": nbytes, "ms_per_step": out,
                       "copy_GB_per_s": nbytes / (copy_ms * 1e-3) / 1e9 if copy_ms > 0 else None,
-                      "pinned_direct_equals_device": same,
+                      "host_routes_equal_device": same, "default_host_parts": default_parts,
                       "timing": "device time per step, CUDA events, median; L2 not flushed"}), flush=True)
     return 0
 

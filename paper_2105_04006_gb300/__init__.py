@@ -91,7 +91,7 @@ EXPORTS = [
     "lsp_mlp_param_count", "lsp_mlp_workspace_size", "lsp_featurize", "lsp_mlp_forward",
     "lsp_mlp_loss_grad", "lsp_mlp_adamw", "lsp_to_bf16", "lsp_top_classes", "lsp_refine_workspace_size",
     "lsp_refine_windows", "lsp_batch_gls", "lsp_periodogram_gls", "lsp_workspace_size_gls",
-    "lsp_probe_fma_rates", "lsp_plan_autotune_ex",
+    "lsp_probe_fma_rates", "lsp_plan_autotune_ex", "lsp_plan_set_host_parts", "lsp_plan_get_host_parts",
 ]
 
 
@@ -136,6 +136,8 @@ def lib():
             L.lsp_plan_enable_timing.argtypes = [P, i32]
             L.lsp_plan_main_kernel_ms.argtypes = [P, ctypes.POINTER(ctypes.c_float)]
             L.lsp_plan_kernel_count.argtypes = [P, ctypes.POINTER(i32)]
+            L.lsp_plan_set_host_parts.argtypes = [P, i32]
+            L.lsp_plan_get_host_parts.argtypes = [P, i64, ctypes.POINTER(i32)]
             DP = ctypes.POINTER(MlpDims)
             f32 = ctypes.c_float
             L.lsp_mlp_param_count.argtypes = [DP, ctypes.POINTER(i64)]
@@ -387,6 +389,18 @@ class Plan:
     def kernel_count(self) -> int:
         v = ctypes.c_int32()
         _check(lib().lsp_plan_kernel_count(self._h, ctypes.byref(v)))
+        return int(v.value)
+
+    def set_host_parts(self, parts: int):
+        """Object groups of execute_host's periodogram return (0: by size, 1: one
+        pass, n: n groups whose copies overlap the next groups' computation)."""
+        _check(lib().lsp_plan_set_host_parts(self._h, int(parts)))
+
+    def host_parts(self) -> int:
+        """The group count execute_host uses for this plan's full periodogram."""
+        v = ctypes.c_int32()
+        nbytes = self.n_obj * self.grid.n_f * (8 if self.opts.precision == FP64 else 4)
+        _check(lib().lsp_plan_get_host_parts(self._h, nbytes, ctypes.byref(v)))
         return int(v.value)
 
     def peaks_buffer(self, device):

@@ -448,6 +448,14 @@ struct lsp_plan {
   int64_t* d_off = nullptr;
   lsp_peak* d_peaks = nullptr;
   void* d_power = nullptr;
+  // grouped periodogram return of the host entry point
+  int32_t host_parts = 0;  // 0: chosen from the periodogram's size
+  int64_t* d_rel = nullptr;
+  size_t d_rel_cap = 0;
+  std::vector<int64_t> h_rel;
+  cudaStream_t copy_stream = nullptr;
+  std::vector<cudaEvent_t> part_ev;
+  cudaEvent_t copy_done = nullptr;
 };
 
 namespace {
@@ -574,6 +582,82 @@ void cache_store(const char* path, const std::string& key, const lsp_config& c, 
     << "}\n";
 }
 
+// Number of object groups of the host entry point's periodogram return.
+int host_parts_for(const lsp_plan* p, size_t pbytes) {
+  int parts = p->host_parts;
+  if (parts == 0) parts = pbytes >= ((size_t)256 << 20) ? 8 : 1;
+  const int64_t most = p->n_obj / 2;  // every group a batch of >= 2 objects
+  if (parts > most) parts = (int)most;
+  return parts < 1 ? 1 : parts;
+}
+
+// The periodogram return in `parts` contiguous object groups (the overlap of
+// transfers with computation of Section 3.5): each group runs as a batch of its
+// own into its rows of the device power buffer on `s`, and a second stream
+// copies those rows to power_out while the next group computes.  An object's
+// powers and peaks do not depend on the other objects of its batch, so the
+// results equal those of one pass bit for bit.  The groups share the plan's
+// workspace, which only kernels on `s` touch.
+lsp_status execute_host_parts(lsp_plan* p, int parts, const int64_t* offsets, void* power_out,
+                              bool want_peaks, cudaStream_t s) {
+  const Layout& F = p->L;
+  const size_t ysz = F.prec == LSP_FP64 ? 8 : 4;
+  const size_t row = (size_t)F.n_f * ysz;
+  std::vector<Layout> G((size_t)parts);
+  std::vector<int64_t> first((size_t)parts + 1);
+  size_t ws_need = 0;
+  p->h_rel.assign((size_t)(p->n_obj + parts), 0);
+  for (int j = 0; j <= parts; ++j) first[(size_t)j] = p->n_obj * j / parts;
+  for (int j = 0; j < parts; ++j) {
+    const int64_t a = first[(size_t)j], b = first[(size_t)j + 1];
+    for (int64_t i = a; i <= b; ++i) p->h_rel[(size_t)(i + j)] = offsets[i] - offsets[a];
+    lsp_status st = resolve(b - a, offsets[b] - offsets[a], &p->grid, &p->opts, &p->cfg, &G[(size_t)j]);
+    if (st) return st;
+    if (G[(size_t)j].total > ws_need) ws_need = G[(size_t)j].total;
+  }
+  lsp_status st = ensure_ws(p, ws_need);
+  if (st) return st;
+  const size_t rel_bytes = p->h_rel.size() * sizeof(int64_t);
+  if (rel_bytes > p->d_rel_cap) {
+    cudaFree(p->d_rel);
+    p->d_rel = nullptr;
+    p->d_rel_cap = 0;
+    if (cudaMalloc(&p->d_rel, rel_bytes) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(LSP_E_NOMEM, "group offsets of %zu bytes", rel_bytes);
+    }
+    p->d_rel_cap = rel_bytes;
+  }
+  if (!p->copy_stream)
+    LSP_CUDA(cudaStreamCreateWithFlags(&p->copy_stream, cudaStreamNonBlocking), "copy stream");
+  if (!p->copy_done) LSP_CUDA(cudaEventCreateWithFlags(&p->copy_done, cudaEventDisableTiming), "event");
+  while (p->part_ev.size() < (size_t)parts) {
+    cudaEvent_t e;
+    LSP_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "event");
+    p->part_ev.push_back(e);
+  }
+  LSP_CUDA(cudaMemcpyAsync(p->d_rel, p->h_rel.data(), rel_bytes, cudaMemcpyHostToDevice, s), "H2D group offsets");
+  // every group's kernels first, then the copies: a copy into pageable memory
+  // may hold the calling thread until it ends
+  for (int j = 0; j < parts; ++j) {
+    const int64_t a = first[(size_t)j];
+    st = run(G[(size_t)j], p->d_t + offsets[a], (const char*)p->d_y + offsets[a] * ysz, p->d_rel + a + j,
+             (char*)p->d_power + a * row, want_peaks ? p->d_peaks + a * p->opts.top_k : nullptr, p->ws, s);
+    if (st) return st;
+    LSP_CUDA(cudaEventRecord(p->part_ev[(size_t)j], s), "group event");
+  }
+  for (int j = 0; j < parts; ++j) {
+    const int64_t a = first[(size_t)j], b = first[(size_t)j + 1];
+    LSP_CUDA(cudaStreamWaitEvent(p->copy_stream, p->part_ev[(size_t)j], 0), "copy wait");
+    LSP_CUDA(cudaMemcpyAsync((char*)power_out + a * row, (const char*)p->d_power + a * row, (b - a) * row,
+                             cudaMemcpyDeviceToHost, p->copy_stream),
+             "D2H power group");
+  }
+  LSP_CUDA(cudaEventRecord(p->copy_done, p->copy_stream), "copy event");
+  LSP_CUDA(cudaStreamWaitEvent(s, p->copy_done, 0), "join copies");
+  return LSP_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -620,6 +704,10 @@ void lsp_plan_destroy(lsp_plan* p) {
   cudaFree(p->d_off);
   cudaFree(p->d_peaks);
   cudaFree(p->d_power);
+  cudaFree(p->d_rel);
+  for (cudaEvent_t e : p->part_ev) cudaEventDestroy(e);
+  if (p->copy_done) cudaEventDestroy(p->copy_done);
+  if (p->copy_stream) cudaStreamDestroy(p->copy_stream);
   delete p;
 }
 
@@ -736,9 +824,19 @@ lsp_status lsp_plan_execute_host(lsp_plan* p, const double* t, const void* y,
       power_direct = attr.devicePointer;
     cudaGetLastError();
   }
+  const int parts = power_out ? host_parts_for(p, pbytes) : 1;
+  if (parts > 1) power_direct = nullptr;
   if (power_out && !power_direct && (st = alloc(&p->d_power, pbytes))) return st;
   LSP_CUDA(cudaMemcpyAsync(p->d_t, t, p->total_nt * sizeof(double), cudaMemcpyHostToDevice, s), "H2D t");
   LSP_CUDA(cudaMemcpyAsync(p->d_y, y, p->total_nt * ysz, cudaMemcpyHostToDevice, s), "H2D y");
+  if (parts > 1) {
+    if ((st = execute_host_parts(p, parts, offsets, power_out, peaks != nullptr, s))) return st;
+    if (peaks)
+      LSP_CUDA(cudaMemcpyAsync(peaks, p->d_peaks, n_peaks * sizeof(lsp_peak), cudaMemcpyDeviceToHost, s),
+               "D2H peaks");
+    LSP_CUDA(cudaStreamSynchronize(s), "synchronize");
+    return LSP_OK;
+  }
   const int64_t* d_off = nullptr;
   if (offsets) {
     LSP_CUDA(cudaMemcpyAsync(p->d_off, offsets, (p->n_obj + 1) * sizeof(int64_t),
@@ -755,6 +853,21 @@ lsp_status lsp_plan_execute_host(lsp_plan* p, const double* t, const void* y,
   if (power_out && !power_direct)
     LSP_CUDA(cudaMemcpyAsync(power_out, p->d_power, pbytes, cudaMemcpyDeviceToHost, s), "D2H power");
   LSP_CUDA(cudaStreamSynchronize(s), "synchronize");
+  return LSP_OK;
+}
+
+lsp_status lsp_plan_set_host_parts(lsp_plan* p, int32_t parts) {
+  g_err.clear();
+  if (!p) return fail(LSP_E_ARG, "plan is NULL");
+  if (parts < 0) return fail(LSP_E_ARG, "parts must be >= 0");
+  p->host_parts = parts;
+  return LSP_OK;
+}
+
+lsp_status lsp_plan_get_host_parts(const lsp_plan* p, int64_t power_bytes, int32_t* parts) {
+  if (!p || !parts) return fail(LSP_E_ARG, "NULL argument");
+  if (power_bytes < 0) return fail(LSP_E_ARG, "power_bytes must be >= 0");
+  *parts = host_parts_for(p, (size_t)power_bytes);
   return LSP_OK;
 }
 

@@ -484,6 +484,71 @@ def test_periodogram_written_to_pinned_host_memory(env, small_batch):
     plan.close()
 
 
+@pytest.mark.parametrize("parts", [2, 3, 7])
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_periodogram_returned_in_object_groups(env, small_batch, precision, parts):
+    """The host entry point's grouped return (copies of one group's rows overlap
+    the next groups' kernels, Section 3.5): the same powers and peaks as one
+    pass, bit for bit, into pageable and page-locked power_out; 40 objects in
+    2, 3 or 7 groups of unequal observation counts."""
+    lsp, torch, dev = env
+    b, ref = small_batch
+    g = lsp.Grid(b.grid.f_min, b.grid.f_max, b.grid.n_f)
+    ydt = np.float32 if precision == "fp32" else np.float64
+    tdt = torch.float32 if precision == "fp32" else torch.float64
+    yh = b.y.astype(ydt)
+    plan = lsp.Plan(b.n_obj, b.t.size, g, precision=precision, top_k=3)
+    plan.set_host_parts(1)
+    assert plan.host_parts() == 1
+    one = np.full((b.n_obj, g.n_f), -1.0, dtype=ydt)
+    pk1 = plan.execute_host(b.t, yh, b.offsets, power=one)
+    err = np.max(np.abs(one.astype(np.float64) - ref[precision]["power"]))
+    assert err <= (TOL32 if precision == "fp32" else TOL64), err
+    plan.set_host_parts(parts)
+    assert plan.host_parts() == parts
+    pag = np.full((b.n_obj, g.n_f), -1.0, dtype=ydt)
+    pk2 = plan.execute_host(b.t, yh, b.offsets, power=pag)
+    pin = torch.full((b.n_obj, g.n_f), -1.0, dtype=tdt).pin_memory()
+    pk3 = plan.execute_host(b.t, yh, b.offsets, power=pin)
+    np.testing.assert_array_equal(pag, one)
+    np.testing.assert_array_equal(pin.numpy(), one)
+    for pk in (pk2, pk3):
+        for name in lsp.PEAK_DTYPE.names:
+            np.testing.assert_array_equal(pk[name], pk1[name], err_msg=name)
+    # the graph-replayed device path still agrees after the grouped calls
+    t = _dev(torch, dev, b.t, torch.float64)
+    y = _dev(torch, dev, yh, tdt)
+    off = _dev(torch, dev, b.offsets, torch.int64)
+    p_dev = torch.empty((b.n_obj, g.n_f), dtype=tdt, device=dev)
+    plan.execute(t, y, off, power=p_dev)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(p_dev.cpu().numpy(), one)
+    plan.close()
+
+
+def test_host_group_count_rule(env, small_batch):
+    """Clamp to n_obj / 2, one pass below 256 MiB by default, one-object plans
+    in one pass, negative counts rejected."""
+    lsp, torch, dev = env
+    b, _ = small_batch
+    g = lsp.Grid(b.grid.f_min, b.grid.f_max, b.grid.n_f)
+    plan = lsp.Plan(b.n_obj, b.t.size, g)
+    assert plan.host_parts() == 1
+    import ctypes
+    v = ctypes.c_int32()
+    assert lsp.lib().lsp_plan_get_host_parts(plan._h, 256 << 20, ctypes.byref(v)) == 0
+    assert v.value == 8
+    plan.set_host_parts(100)
+    assert plan.host_parts() == b.n_obj // 2
+    with pytest.raises(lsp.LSPError):
+        plan.set_host_parts(-1)
+    plan.close()
+    one = lsp.Plan(1, 500, g)
+    one.set_host_parts(4)
+    assert one.host_parts() == 1
+    one.close()
+
+
 def test_fma_rate_probe_is_plausible(env):
     # ceilings for the roofline fractions: below the nominal unit counts at the
     # highest SM clock of the part (2.07 GHz), and not far below them
