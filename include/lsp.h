@@ -192,8 +192,10 @@ lsp_status lsp_batch_noalloc(const double* t, const void* y, const int64_t* offs
  * type and layout (NULL: unit weights).  Objects need at least three
  * observations; a non-positive or non-finite dy flags LSP_FLAG_NONFINITE.
  * Arguments otherwise as lsp_batch / lsp_periodogram; the workspace size
- * comes from lsp_workspace_size_gls.  There is no split-N_t for a single
- * object here.
+ * comes from lsp_workspace_size_gls.  A single object is split over its
+ * observations as in lsp_periodogram (opts.obs_split; automatic: every
+ * partial sum over at most 8192 observations, and enough items for all SMs),
+ * the six weighted sums of the slices added in a fixed order.
  */
 lsp_status lsp_workspace_size_gls(int64_t n_obj, int64_t total_nt, const lsp_grid* grid,
                                   const lsp_opts* opts, size_t* bytes);

@@ -298,6 +298,29 @@ def workspace_size_gls(n_obj, total_nt, grid: Grid, opts: Opts) -> int:
     return int(n.value)
 
 
+def periodogram_gls(t, y, dy, grid: Grid, *, return_power=True, workspace=None, **kw):
+    """Generalized periodogram of one object (photometric errors dy, floating
+    mean), split over its observations like ``periodogram``.  Returns (power or
+    None, peaks)."""
+    torch = _torch()
+    opts = make_opts(**kw)
+    _require(t, "t", torch.float64)
+    _require(y, "y", _dtypes(opts), t.device)
+    if dy is not None:
+        _require(dy, "dy", _dtypes(opts), t.device)
+    n_t = t.numel()
+    if y.numel() != n_t or (dy is not None and dy.numel() != n_t):
+        raise ValueError("t, y and dy differ in length")
+    ws_bytes = workspace_size_gls(1, n_t, grid, opts)
+    ws = workspace if workspace is not None else torch.empty(max(ws_bytes, 256), dtype=torch.uint8,
+                                                                device=t.device)
+    power = torch.empty(grid.n_f, dtype=_dtypes(opts), device=t.device) if return_power else None
+    peaks = torch.empty(opts.top_k * 40, dtype=torch.uint8, device=t.device)
+    _check(lib().lsp_periodogram_gls(_ptr(t), _ptr(y), _ptr(dy), n_t, ctypes.byref(grid), ctypes.byref(opts),
+                                     _ptr(power), _ptr(peaks), _ptr(ws), ws.numel(), _stream_handle(t.device)))
+    return power, peaks
+
+
 def batch_gls(t, y, dy, offsets, grid: Grid, *, return_power=False, workspace=None, **kw):
     """Generalized periodogram of a CSR batch (photometric errors dy, floating mean).
 

@@ -158,7 +158,7 @@ lsp_status resolve(int64_t n_obj, int64_t total_nt, const lsp_grid* g, const lsp
   const int64_t chunk = (int64_t)threads * fpt;
   l.n_chunks = (int32_t)((l.n_f + chunk - 1) / chunk);
   int split = 1;
-  if (n_obj == 1 && !gls) {  // the generalized kernels have no split-N_t combine
+  if (n_obj == 1) {
     if (split_req > 0) {
       split = split_req;
     } else {
@@ -190,7 +190,8 @@ lsp_status resolve(int64_t n_obj, int64_t total_nt, const lsp_grid* g, const lsp
   l.off_queue = take(16);
   l.off_best = take((size_t)n_obj * l.n_res_chunks * sizeof(ChunkBest));
   l.off_cand = take(l.top ? (size_t)n_obj * l.n_res_chunks * sizeof(ChunkCand) : 0);
-  l.off_part = take(split > 1 ? (size_t)split * l.n_f * 4 * (l.prec ? 8 : 4) : 0);
+  // partial sums: 4 per frequency, the generalized periodogram's 6 in slots of 8
+  l.off_part = take(split > 1 ? (size_t)split * l.n_f * (gls ? 8 : 4) * (l.prec ? 8 : 4) : 0);
   l.off_stats = take(n_obj == 1 ? stats_slices_bytes(total_nt) : 0);
   l.total = off;
 
@@ -260,7 +261,7 @@ lsp_status run(const Layout& L, const double* t, const void* y, const int64_t* o
   const bool fused = L.split > 1 && !L.top && peaks;
   if (L.split > 1)
     LSP_CUDA(launch_combine(L.prec, part, L.split, L.n_f, obj, rec, power_out, best, cand, st,
-                            fused ? peaks : nullptr, L.f_min, L.df, queue + 2),
+                            fused ? peaks : nullptr, L.f_min, L.df, queue + 2, L.gls != 0),
              "split combine");
   if (peaks && !fused)
     LSP_CUDA(launch_finalize(obj, best, cand, L.n_obj, L.n_res_chunks, L.top_k, L.f_min, L.df,

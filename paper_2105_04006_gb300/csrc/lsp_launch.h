@@ -76,7 +76,8 @@ int main_blocks_per_sm(int prec, int packed, int k_reseed, int fpt, int threads,
                       int abl = 0);
 size_t main_dyn_smem(int prec, int fpt, int threads, int top);
 
-// Split-N_t combine (single object): sums the partial sums in a fixed order,
+// Split-N_t combine (single object; gls: the generalized periodogram's six
+// sums in stride-8 slots): sums the partial sums in a fixed order,
 // evaluates the power, stores it (optional) and reduces chunk results; with
 // peaks, no candidates and a zeroed ticket word it also writes the first
 // maximum (no finalize launch needed).
@@ -85,7 +86,7 @@ constexpr int kCombinePerThread = 4;
 cudaError_t launch_combine(int prec, const void* part, int split, int64_t n_f, const ObjInfo* obj,
                            const void* rec, void* power_out, ChunkBest* best, ChunkCand* cand,
                            cudaStream_t stream, lsp_peak* peaks = nullptr, double f_min = 0.0,
-                           double df = 0.0, uint32_t* ticket = nullptr);
+                           double df = 0.0, uint32_t* ticket = nullptr, bool gls = false);
 
 // Per-object peaks from the chunk results.
 cudaError_t launch_finalize(const ObjInfo* obj, const ChunkBest* best, const ChunkCand* cand,

@@ -71,6 +71,21 @@ __device__ __forceinline__ void store_part(double* part, int64_t idx, double a, 
   p2[1] = make_double2(c, d);
 }
 
+// The six generalized sums of one frequency in a stride-8 slot (two 16-byte
+// words for FP32, three for FP64; the last two entries stay unused).
+__device__ __forceinline__ void store_part_gls(float* part, int64_t idx, float a, float b, float c, float d,
+                                               float e, float f) {
+  reinterpret_cast<float4*>(part)[2 * idx] = make_float4(a, b, c, d);
+  reinterpret_cast<float2*>(part)[4 * idx + 2] = make_float2(e, f);
+}
+__device__ __forceinline__ void store_part_gls(double* part, int64_t idx, double a, double b, double c,
+                                               double d, double e, double f) {
+  double2* p2 = reinterpret_cast<double2*>(part) + 4 * idx;
+  p2[0] = make_double2(a, b);
+  p2[1] = make_double2(c, d);
+  p2[2] = make_double2(e, f);
+}
+
 // Item decoding shared by the kernels.
 struct Item {
   int64_t o;
@@ -416,7 +431,7 @@ __global__ void __launch_bounds__(256) main_f32_packed_gls(MainParams<RecF32, fl
   float* s_pw = reinterpret_cast<float*>(dyn_smem);
   const int tid = threadIdx.x;
   const uint32_t n_items = p.n_items_dev ? *p.n_items_dev : (uint32_t)p.n_items;
-  const uint32_t n_chunks = (uint32_t)p.n_chunks;
+  const uint32_t split = (uint32_t)p.split, n_chunks = (uint32_t)p.n_chunks;
 
   for (;;) {
     if (tid == 0) s_item = atomicAdd(p.queue, 1u);
@@ -424,14 +439,17 @@ __global__ void __launch_bounds__(256) main_f32_packed_gls(MainParams<RecF32, fl
     const uint32_t item = s_item;
     __syncthreads();
     if (item >= n_items) break;
-    const uint32_t chunk = item % n_chunks;
-    const uint32_t orank = item / n_chunks;
+    const uint32_t is = item % split;
+    const uint32_t oc = item / split;
+    const uint32_t chunk = oc % n_chunks;
+    const uint32_t orank = oc / n_chunks;
     const int64_t o = p.order ? (int64_t)p.order[orank] : (int64_t)orank;
     const ObjInfo oi = p.obj[o];
     const int64_t kc0 = (int64_t)chunk * blockDim.x * F;
     const uint32_t k0 = (uint32_t)(kc0 + (int64_t)tid * F);
-    const int64_t ob = oi.begin;
-    const int64_t oe = oi.flags ? ob : oi.begin + oi.n;
+    const int64_t ob = oi.begin + (int64_t)oi.n * is / split;
+    int64_t oe = oi.begin + (int64_t)oi.n * (is + 1) / split;
+    if (oi.flags) oe = ob;  // flagged objects: zero power
 
     f2_t xc[K], xs[K], cw[K], sw[K], cc[K], cs[K];
 #pragma unroll
@@ -464,6 +482,26 @@ __global__ void __launch_bounds__(256) main_f32_packed_gls(MainParams<RecF32, fl
         for (int j = n_ch; j < nt; ++j) obs(s_ent[j], std::false_type{});
       }
       __syncthreads();
+    }
+
+    if (split > 1) {  // one slice of a single object: partial sums for the combine
+      float* part = p.part + (int64_t)is * p.n_f * 8;
+#pragma unroll
+      for (int m = 0; m < K; ++m) {
+        float v[2][6];
+        f2_unpack(xc[m], v[0][0], v[1][0]);
+        f2_unpack(xs[m], v[0][1], v[1][1]);
+        f2_unpack(cw[m], v[0][2], v[1][2]);
+        f2_unpack(sw[m], v[0][3], v[1][3]);
+        f2_unpack(cc[m], v[0][4], v[1][4]);
+        f2_unpack(cs[m], v[0][5], v[1][5]);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int64_t k = (int64_t)k0 + h * K + m;
+          if (k < p.n_f) store_part_gls(part, k, v[h][0], v[h][1], v[h][2], v[h][3], v[h][4], v[h][5]);
+        }
+      }
+      continue;
     }
 
     float pv[F];
@@ -514,14 +552,15 @@ __global__ void __launch_bounds__(256) main_f64_gls(MainParams<RecF64, double> p
     const int64_t item = s_item;
     __syncthreads();
     if (item >= p.n_items) break;
-    const int chunk = (int)(item % p.n_chunks);
-    const int64_t orank = item / p.n_chunks;
-    const int64_t o = p.order ? (int64_t)p.order[orank] : orank;
+    const Item it = decode_item(p, item);
+    const int64_t o = it.o;
+    const int chunk = it.chunk;
     const ObjInfo oi = p.obj[o];
     const int64_t kc0 = (int64_t)chunk * blockDim.x * F;
     const uint32_t k0 = (uint32_t)(kc0 + (int64_t)tid * F);
-    const int64_t ob = oi.begin;
-    const int64_t oe = oi.flags ? ob : oi.begin + oi.n;
+    const int64_t ob = oi.begin + (int64_t)oi.n * it.s / p.split;
+    int64_t oe = oi.begin + (int64_t)oi.n * (it.s + 1) / p.split;
+    if (oi.flags) oe = ob;  // flagged objects: zero power
     double xc[K], xs[K], cw[K], sw[K], cc[K], cs[K];
 #pragma unroll
     for (int m = 0; m < K; ++m) xc[m] = xs[m] = cw[m] = sw[m] = cc[m] = cs[m] = 0.0;
@@ -548,6 +587,14 @@ __global__ void __launch_bounds__(256) main_f64_gls(MainParams<RecF64, double> p
         });
       }
       __syncthreads();
+    }
+    if (p.split > 1) {  // one slice of a single object: partial sums for the combine
+      double* part = p.part + (int64_t)it.s * p.n_f * 8;
+#pragma unroll
+      for (int m = 0; m < K; ++m)
+        if ((int64_t)k0 + m < p.n_f)
+          store_part_gls(part, (int64_t)k0 + m, xc[m], xs[m], cw[m], sw[m], cc[m], cs[m]);
+      continue;
     }
     double pv[F];
 #pragma unroll

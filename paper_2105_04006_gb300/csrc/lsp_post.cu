@@ -60,8 +60,9 @@ __device__ __forceinline__ lsp_peak make_peak(int64_t k, double p, double f_min,
 // fixed order s = 0..S-1 (deterministic), then Eq. 2 and the chunk results.
 // With peaks (first maximum only), the last CTA to finish (ticket, zero on
 // entry) also reduces all chunk results in index order and writes the peak,
-// so no separate finalize launch follows.
-template <typename Real>
+// so no separate finalize launch follows.  GLS: the six weighted sums of the
+// generalized periodogram (Section 4.11) in stride-8 slots, and its power.
+template <typename Real, bool GLS>
 __global__ void __launch_bounds__(kCombineThreads) combine_kernel(
     const Real* __restrict__ part, int split, int64_t n_f, const ObjInfo* __restrict__ obj,
     const RecF32* __restrict__ rec, Real* __restrict__ power_out, ChunkBest* __restrict__ best,
@@ -81,6 +82,26 @@ __global__ void __launch_bounds__(kCombineThreads) combine_kernel(
 #pragma unroll
   for (int m = 0; m < NP; ++m) {
     const int64_t k = k0 + m;
+    if constexpr (GLS) {
+      Real v[6] = {0, 0, 0, 0, 0, 0};
+      if (k < n_f && !oi.flags) {
+        for (int s = 0; s < split; ++s) {
+          const Real* q = part + ((int64_t)s * n_f + k) * 8;
+#pragma unroll
+          for (int j = 0; j < 6; ++j) v[j] += q[j];
+        }
+      }
+      bool ill;
+      if constexpr (std::is_same<Real, float>::value) {
+        pv[m] = oi.norm_scale_f * gls_power<float>(v[0], v[1], v[2], v[3], v[4], v[5], oi.wsum_f,
+                                                   (float)oi.sum_y2, EpsRel<float>::v, ill);
+        if (k < n_f && !oi.flags && ill) bad |= 1u << m;
+      } else {
+        pv[m] = oi.norm_scale * gls_power<double>(v[0], v[1], v[2], v[3], v[4], v[5], oi.wsum, oi.sum_y2,
+                                                  EpsRel<double>::v, ill);
+      }
+      continue;
+    }
     Real xc = 0, xs = 0, cc = 0, cs = 0;
     if (k < n_f && !oi.flags) {
       for (int s = 0; s < split; ++s) {
@@ -99,8 +120,12 @@ __global__ void __launch_bounds__(kCombineThreads) combine_kernel(
       pv[m] = oi.flags ? Real(0) : scale * lsp_power<Real>(xc, xs, cc, cs, nf, EpsRel<Real>::v);
     }
   }
-  if constexpr (std::is_same<Real, float>::value)
-    fix_ill_conditioned<NP>(pv, bad, (uint32_t)k0, rec, oi.begin, oi.n, oi.norm_scale);
+  if constexpr (std::is_same<Real, float>::value) {
+    if constexpr (GLS)
+      fix_ill_conditioned_gls<NP>(pv, bad, (uint32_t)k0, rec, oi);
+    else
+      fix_ill_conditioned<NP>(pv, bad, (uint32_t)k0, rec, oi.begin, oi.n, oi.norm_scale);
+  }
   if (power_out) {
 #pragma unroll
     for (int m = 0; m < NP; ++m)
@@ -334,20 +359,29 @@ cudaError_t launch_max_abs_diff(const float* a, const double* b, int64_t n, doub
 
 cudaError_t launch_combine(int prec, const void* part, int split, int64_t n_f, const ObjInfo* obj,
                            const void* rec, void* power_out, ChunkBest* best, ChunkCand* cand,
-                           cudaStream_t stream, lsp_peak* peaks, double f_min, double df, uint32_t* ticket) {
+                           cudaStream_t stream, lsp_peak* peaks, double f_min, double df, uint32_t* ticket,
+                           bool gls) {
   const int64_t per_cta = (int64_t)kCombineThreads * kCombinePerThread;
   const unsigned grid = (unsigned)((n_f + per_cta - 1) / per_cta);
   // chunk_results keeps the chunk's powers in shared memory (FP32: one
   // padding word per thread)
   const size_t dyn = cand ? (prec ? (size_t)per_cta * 8 : (size_t)kCombineThreads * (kCombinePerThread + 1) * 4) : 0;
   if (cand || !ticket) peaks = nullptr;  // top-k peaks: the separate finalize
-  if (prec)
-    combine_kernel<double><<<grid, kCombineThreads, dyn, stream>>>(
-        (const double*)part, split, n_f, obj, nullptr, (double*)power_out, best, cand, peaks, f_min, df, ticket);
-  else
-    combine_kernel<float><<<grid, kCombineThreads, dyn, stream>>>(
-        (const float*)part, split, n_f, obj, (const RecF32*)rec, (float*)power_out, best, cand, peaks, f_min,
-        df, ticket);
+  auto go = [&](auto kern, const auto* pt, const RecF32* r, auto* pw) {
+    kern<<<grid, kCombineThreads, dyn, stream>>>(pt, split, n_f, obj, r, pw, best, cand, peaks, f_min, df,
+                                                 ticket);
+  };
+  if (prec) {
+    if (gls)
+      go(combine_kernel<double, true>, (const double*)part, nullptr, (double*)power_out);
+    else
+      go(combine_kernel<double, false>, (const double*)part, nullptr, (double*)power_out);
+  } else {
+    if (gls)
+      go(combine_kernel<float, true>, (const float*)part, (const RecF32*)rec, (float*)power_out);
+    else
+      go(combine_kernel<float, false>, (const float*)part, (const RecF32*)rec, (float*)power_out);
+  }
   return cudaGetLastError();
 }
 

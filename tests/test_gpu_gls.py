@@ -102,6 +102,68 @@ def test_gls_single_object_entry_point(env):
     assert abs(int(lsp.peaks_to_numpy(peaks)["idx"][0]) - int(ref["arg_idx"][0])) <= 1
 
 
+def _single_gls(env, t, y, dy, grid, precision, **kw):
+    lsp, torch, dev = env
+    dt = torch.float32 if precision == "fp32" else torch.float64
+    g = lsp.Grid(grid.f_min, grid.f_max, grid.n_f)
+    p, pk = lsp.periodogram_gls(torch.tensor(t, dtype=torch.float64, device=dev),
+                                torch.tensor(y, dtype=dt, device=dev),
+                                torch.tensor(dy, dtype=dt, device=dev), g, precision=precision, **kw)
+    torch.cuda.synchronize()
+    return p.cpu().numpy().astype(np.float64), lsp.peaks_to_numpy(pk)
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+@pytest.mark.parametrize("split", [0, 2, 5, 16])
+def test_gls_single_object_split_over_observations(env, precision, split):
+    """One object's observations in slices (automatic or 2, 5, 16): the six
+    weighted sums of the slices added in a fixed order, then the power."""
+    b = synth.single_small(n_t=3001, grid=synth.Grid(0.1, 10.0, 7001))
+    dy = np.random.default_rng(5).uniform(0.05, 0.2, b.t.size)
+    p, pk = _single_gls(env, b.t, b.y, dy, b.grid, precision, obs_split=split)
+    ref = oracle.gls_batch(b.t, _seen(b.y, precision), _seen(dy, precision), b.offsets, b.grid.f_min,
+                           b.grid.f_max, b.grid.n_f)
+    err = np.max(np.abs(p - ref["power"][0]))
+    assert err <= TOL[precision], err
+    if precision == "fp64":
+        assert pk["idx"][0] == ref["arg_idx"][0]
+    else:
+        assert abs(int(pk["idx"][0]) - int(ref["arg_idx"][0])) <= 1
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_gls_single_large_object(env, precision):
+    """50000 observations (automatic split: 256 slices of about 195) against
+    the oracle on the whole grid, and the peak's period."""
+    b = synth.single_large(n_t=50_000, grid=synth.Grid(0.05, 25.0, 3001))
+    dy = np.random.default_rng(6).uniform(0.1, 0.3, b.t.size)
+    p, pk = _single_gls(env, b.t, b.y, dy, b.grid, precision)
+    ref = oracle.gls_batch(b.t, _seen(b.y, precision), _seen(dy, precision), b.offsets, b.grid.f_min,
+                           b.grid.f_max, b.grid.n_f)
+    err = np.max(np.abs(p - ref["power"][0]))
+    assert err <= TOL[precision], err
+    assert abs(int(pk["idx"][0]) - int(ref["arg_idx"][0])) <= (0 if precision == "fp64" else 1)
+    assert pk["period"][0] == pytest.approx(1.0 / (b.grid.f_min + pk["idx"][0] * b.grid.df), rel=1e-12)
+
+
+def test_gls_single_object_split_ill_conditioned_bins(env):
+    """Nightly one-hour windows: the daily aliases are ill-conditioned, so the
+    combine re-evaluates them in FP64 as the unsplit kernel does."""
+    rng = np.random.default_rng(12)
+    n = 600
+    nights = np.sort(rng.choice(3000, n, replace=False)).astype(np.float64)
+    t = 60000.0 + nights + 0.3 + rng.uniform(0, 1 / 24, n)
+    y = 0.4 * np.sin(2 * np.pi * 1.37 * t) + rng.normal(0, 0.2, n) + 3.0
+    dy = rng.uniform(0.05, 0.3, n)
+    grid = synth.Grid(0.24, 12.0, 20011)
+    off = np.array([0, n], dtype=np.int64)
+    ref = oracle.gls_batch(t, _seen(y, "fp32"), _seen(dy, "fp32"), off, grid.f_min, grid.f_max, grid.n_f)
+    for split in (1, 4):
+        p, pk = _single_gls(env, t, y, dy, grid, "fp32", obs_split=split)
+        assert np.max(np.abs(p - ref["power"][0])) <= 1e-4, split
+        assert abs(int(pk["idx"][0]) - int(ref["arg_idx"][0])) <= 1
+
+
 def test_gls_degenerate_objects_and_nightly_cadence(env):
     rng = np.random.default_rng(9)
     segs = [(np.array([60000.0, 60001.0]), np.array([1.0, 2.0]), np.array([0.1, 0.1])),   # two obs
