@@ -90,13 +90,20 @@ class ClockSampler:
         except (FileNotFoundError, OSError):
             self.proc = None
             return
+        self.first = threading.Event()
         self.thread = threading.Thread(target=self._read, daemon=True)
         self.thread.start()
+        # nvidia-smi's start-up (NVML initialisation) can hold up the GPU work
+        # launched meanwhile for about a second: the timed region starts only
+        # after its first sample has arrived
+        self.first.wait(timeout=10.0)
         time.sleep(0.3)
 
     def _read(self):
         for line in self.proc.stdout:
             self.rows.append((time.time(), [x.strip() for x in line.split(",")]))
+            self.first.set()
+        self.first.set()
 
     def mark(self, which):
         if which == 0:

@@ -60,3 +60,58 @@ def test_warmup_below_three_is_refused():
     out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--warmup", "1"],
                          capture_output=True, text=True, timeout=120, cwd=ROOT)
     assert out.returncode != 0 and "warmup" in out.stderr
+
+
+def test_clock_sampler_waits_for_the_first_sample(monkeypatch):
+    """The timed region starts only after nvidia-smi has printed its first row,
+    and the summary takes the rows inside the marked region."""
+    import io
+    import subprocess
+    import threading
+    import time
+    import bench
+
+    release = threading.Event()
+    row = "0, 2070, 2070, 500.0, 0x0, Not Active, Not Active, Not Active, Active\n"
+
+    class SlowOut(io.TextIOBase):
+        def __init__(self):
+            self.n = 0
+
+        def __iter__(self):
+            return self
+
+        def __next__(self):
+            if self.n == 0:
+                release.wait(5.0)  # start-up: nothing printed yet
+            if self.n >= 6:
+                raise StopIteration
+            self.n += 1
+            time.sleep(0.02)
+            return row
+
+    class FakeProc:
+        def __init__(self, *a, **k):
+            self.stdout = SlowOut()
+
+        def terminate(self):
+            pass
+
+        def wait(self, timeout=None):
+            return 0
+
+        def kill(self):
+            pass
+
+    monkeypatch.setattr(subprocess, "Popen", FakeProc)
+    clk = bench.ClockSampler("0")
+    threading.Timer(0.5, release.set).start()
+    t0 = time.time()
+    clk.start()
+    assert time.time() - t0 >= 0.5  # returned only after the first row
+    clk.mark(0)
+    time.sleep(0.2)
+    clk.mark(1)
+    got = clk.stop()
+    assert got["sm_mhz"] == 2070.0 and got["sm_max_mhz"] == 2070.0
+    assert got["reasons"] == ["sw_power_cap"] and got["power_w_max"] == 500.0
