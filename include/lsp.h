@@ -288,7 +288,9 @@ lsp_status lsp_plan_execute_host(lsp_plan* plan, const double* t, const void* y,
  * equal those of one pass bit for bit.  parts = 0 (the default): 8 groups
  * for periodograms of at least 256 MiB, else one pass.  The count is clamped
  * to n_obj / 2 (every group has two objects or more; a one-object plan always
- * runs in one pass).  Without power_out the setting has no effect.
+ * runs in one pass).  Without power_out the setting has no effect, and
+ * offsets that are not monotonic inside [0, total_nt] take the one-pass route
+ * (which flags the objects they touch).
  * Errors: LSP_E_ARG for a NULL plan or parts < 0.
  */
 lsp_status lsp_plan_set_host_parts(lsp_plan* plan, int32_t parts);

@@ -825,7 +825,14 @@ lsp_status lsp_plan_execute_host(lsp_plan* p, const double* t, const void* y,
       power_direct = attr.devicePointer;
     cudaGetLastError();
   }
-  const int parts = power_out ? host_parts_for(p, pbytes) : 1;
+  int parts = power_out ? host_parts_for(p, pbytes) : 1;
+  if (parts > 1) {
+    // groups index t and y by the offsets: they need monotonic offsets inside
+    // the inputs (others take the one-pass route, which flags the objects)
+    bool ok = offsets[0] >= 0 && offsets[p->n_obj] <= p->total_nt;
+    for (int64_t i = 0; ok && i < p->n_obj; ++i) ok = offsets[i] <= offsets[i + 1];
+    if (!ok) parts = 1;
+  }
   if (parts > 1) power_direct = nullptr;
   if (power_out && !power_direct && (st = alloc(&p->d_power, pbytes))) return st;
   LSP_CUDA(cudaMemcpyAsync(p->d_t, t, p->total_nt * sizeof(double), cudaMemcpyHostToDevice, s), "H2D t");

@@ -526,6 +526,32 @@ def test_periodogram_returned_in_object_groups(env, small_batch, precision, part
     plan.close()
 
 
+def test_host_groups_with_bad_offsets_take_one_pass(env):
+    """Offsets that run backwards or past the inputs: the grouped return falls
+    back to one pass, which flags the objects they touch (no group reads past
+    the inputs)."""
+    lsp, torch, dev = env
+    b = synth.ragged_survey(8, seed=8, grid=synth.Grid(0.5, 2.0, 301))
+    bad = b.offsets.copy()
+    bad[2], bad[3] = bad[3], bad[2]
+    bad[8] = bad[8] + 7
+    g = lsp.Grid(b.grid.f_min, b.grid.f_max, b.grid.n_f)
+    yh = b.y.astype(np.float32)
+    plan = lsp.Plan(b.n_obj, b.t.size, g)
+    one = np.full((b.n_obj, g.n_f), -1.0, dtype=np.float32)
+    plan.set_host_parts(1)
+    pk1 = plan.execute_host(b.t, yh, bad, power=one)
+    grp = np.full((b.n_obj, g.n_f), -1.0, dtype=np.float32)
+    plan.set_host_parts(4)
+    pk2 = plan.execute_host(b.t, yh, bad, power=grp)
+    np.testing.assert_array_equal(grp, one)
+    for name in lsp.PEAK_DTYPE.names:
+        np.testing.assert_array_equal(pk2[name], pk1[name], err_msg=name)
+    assert pk1["flags"][2] & lsp.FLAG_BAD_OFFSETS and pk1["flags"][7] & lsp.FLAG_BAD_OFFSETS
+    assert not (pk1["flags"][0] & lsp.FLAG_BAD_OFFSETS)
+    plan.close()
+
+
 def test_host_group_count_rule(env, small_batch):
     """Clamp to n_obj / 2, one pass below 256 MiB by default, one-object plans
     in one pass, negative counts rejected."""
