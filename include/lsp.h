@@ -343,7 +343,10 @@ lsp_status lsp_plan_autotune_ex(lsp_plan* plan, const double* t, const void* y, 
  * CUDA events on its stream, around the main (trig-sum) kernel, inside the
  * captured graph.  lsp_plan_main_kernel_ms waits for the last execution's
  * second event and returns the main kernel's duration in milliseconds.
- * Enabling or disabling re-captures the graph on the next execution.
+ * Enabling or disabling re-captures the graph on the next execution.  A host
+ * call that returns the periodogram in object groups (lsp_plan_set_host_parts)
+ * runs outside the graph and records no events: the probe keeps describing
+ * the last graph execution.
  */
 lsp_status lsp_plan_enable_timing(lsp_plan* plan, int32_t enable);
 lsp_status lsp_plan_main_kernel_ms(lsp_plan* plan, float* ms);
