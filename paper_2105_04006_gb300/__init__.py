@@ -181,18 +181,23 @@ def _ptr(x):
     return ctypes.c_void_p(0 if x is None else x.data_ptr())
 
 
-def _require(x, name, dtype, device=None):
+def _require(x, name, dtype, device=None, numel=None, host_ok=False):
+    """A contiguous tensor of `dtype` (and, if given, exactly `numel` elements:
+    the library reads or writes that many) on a CUDA device; host_ok also
+    admits page-locked host memory, which the kernels address directly."""
     torch = _torch()
     if not isinstance(x, torch.Tensor):
         raise TypeError(f"{name} must be a torch tensor")
     if x.dtype != dtype:
         raise TypeError(f"{name} must be {dtype}, got {x.dtype}")
-    if not x.is_cuda:
-        raise TypeError(f"{name} must be a CUDA tensor")
-    if device is not None and x.device != device:
+    if not x.is_cuda and not (host_ok and x.is_pinned()):
+        raise TypeError(f"{name} must be a CUDA tensor" + (" or page-locked host memory" if host_ok else ""))
+    if device is not None and x.is_cuda and x.device != device:
         raise ValueError(f"{name} is on {x.device}, expected {device}")
     if not x.is_contiguous():
         raise ValueError(f"{name} must be contiguous")
+    if numel is not None and x.numel() != numel:
+        raise ValueError(f"{name} has {x.numel()} elements, expected {numel}")
 
 
 def make_opts(precision="fp32", norm="standard", center=True, top_k=1, k_reseed=0,
@@ -275,7 +280,7 @@ def batch(t, y, offsets, grid: Grid, *, return_power=False, workspace=None, **kw
     torch = _torch()
     opts = make_opts(**kw)
     _require(t, "t", torch.float64)
-    _require(y, "y", _dtypes(opts), t.device)
+    _require(y, "y", _dtypes(opts), t.device, numel=t.numel())
     _require(offsets, "offsets", torch.int64, t.device)
     n_obj = offsets.numel() - 1
     total = t.numel()
@@ -329,9 +334,9 @@ def batch_gls(t, y, dy, offsets, grid: Grid, *, return_power=False, workspace=No
     torch = _torch()
     opts = make_opts(**kw)
     _require(t, "t", torch.float64)
-    _require(y, "y", _dtypes(opts), t.device)
+    _require(y, "y", _dtypes(opts), t.device, numel=t.numel())
     if dy is not None:
-        _require(dy, "dy", _dtypes(opts), t.device)
+        _require(dy, "dy", _dtypes(opts), t.device, numel=t.numel())
     _require(offsets, "offsets", torch.int64, t.device)
     n_obj = offsets.numel() - 1
     ws_bytes = workspace_size_gls(n_obj, t.numel(), grid, opts)
@@ -433,12 +438,19 @@ class Plan:
     def execute(self, t, y, offsets=None, power=None, peaks=None):
         """Run on device tensors; returns the peaks tensor (allocated if not given)."""
         torch = _torch()
-        _require(t, "t", torch.float64)
-        _require(y, "y", _dtypes(self.opts), t.device)
+        _require(t, "t", torch.float64, numel=self.total_nt)
+        _require(y, "y", _dtypes(self.opts), t.device, numel=self.total_nt)
         if offsets is not None:
-            _require(offsets, "offsets", torch.int64, t.device)
+            _require(offsets, "offsets", torch.int64, t.device, numel=self.n_obj + 1)
+        elif self.n_obj > 1:
+            raise ValueError("a batch plan needs offsets")
+        if power is not None:  # device memory, or page-locked host memory written directly
+            _require(power, "power", _dtypes(self.opts), t.device, numel=self.n_obj * self.grid.n_f,
+                     host_ok=True)
         if peaks is None:
             peaks = self.peaks_buffer(t.device)
+        else:
+            _require(peaks, "peaks", torch.uint8, t.device, numel=self.n_obj * self.opts.top_k * 40, host_ok=True)
         _check(lib().lsp_plan_execute(self._h, _ptr(t), _ptr(y), _ptr(offsets), _ptr(power), _ptr(peaks),
                                       _stream_handle(t.device)))
         return peaks
@@ -450,27 +462,43 @@ class Plan:
         synchronises.  Returns the peaks as a structured numpy array.
         """
         torch = _torch()
-        dev = device or torch.device("cuda", torch.cuda.current_device())
+        tdt = {np.float64: torch.float64, np.float32: torch.float32, np.int64: torch.int64}
 
-        def hptr(a, dtype):
+        def hptr(a, dtype, n, name):
+            # the library reads or writes exactly n elements of `dtype` here
             if a is None:
                 return ctypes.c_void_p(0)
             if isinstance(a, np.ndarray):
                 if a.dtype != dtype or not a.flags.c_contiguous:
-                    raise TypeError(f"host array must be contiguous {dtype}")
+                    raise TypeError(f"{name} must be a contiguous {np.dtype(dtype).name} array")
+                if a.size != n:
+                    raise ValueError(f"{name} has {a.size} elements, the plan needs {n}")
                 return ctypes.c_void_p(a.ctypes.data)
-            if a.is_cuda or not a.is_contiguous():
-                raise TypeError("host tensor must be a contiguous CPU tensor")
+            if a.is_cuda or not a.is_contiguous() or a.dtype != tdt[dtype]:
+                raise TypeError(f"{name} must be a contiguous CPU tensor of {tdt[dtype]}")
+            if a.numel() != n:
+                raise ValueError(f"{name} has {a.numel()} elements, the plan needs {n}")
             return ctypes.c_void_p(a.data_ptr())
 
         ydt = np.float64 if self.opts.precision == FP64 else np.float32
+        n_pk = self.n_obj * self.opts.top_k
         if peaks is None:
-            peaks = np.empty(self.n_obj * self.opts.top_k, dtype=PEAK_DTYPE)
-        pk_ptr = (ctypes.c_void_p(peaks.ctypes.data) if isinstance(peaks, np.ndarray)
-                  else ctypes.c_void_p(peaks.data_ptr()))
-        _check(lib().lsp_plan_execute_host(self._h, hptr(t, np.float64), hptr(y, ydt),
-                                           hptr(offsets, np.int64), hptr(power, ydt), pk_ptr,
-                                           _stream_handle(dev)))
+            peaks = np.empty(n_pk, dtype=PEAK_DTYPE)
+        if isinstance(peaks, np.ndarray):
+            if peaks.dtype != PEAK_DTYPE or not peaks.flags.c_contiguous or peaks.size != n_pk:
+                raise TypeError(f"peaks must be a contiguous array of {n_pk} PEAK_DTYPE records")
+            pk_ptr = ctypes.c_void_p(peaks.ctypes.data)
+        else:
+            if peaks.is_cuda or not peaks.is_contiguous() or peaks.numel() * peaks.element_size() != n_pk * 40:
+                raise TypeError(f"peaks must be a contiguous CPU tensor of {n_pk * 40} bytes")
+            pk_ptr = ctypes.c_void_p(peaks.data_ptr())
+        if self.n_obj > 1 and offsets is None:
+            raise ValueError("a batch plan needs offsets")
+        args = (hptr(t, np.float64, self.total_nt, "t"), hptr(y, ydt, self.total_nt, "y"),
+                hptr(offsets, np.int64, self.n_obj + 1, "offsets"),
+                hptr(power, ydt, self.n_obj * self.grid.n_f, "power"), pk_ptr)
+        dev = device or torch.device("cuda", torch.cuda.current_device())
+        _check(lib().lsp_plan_execute_host(self._h, *args, _stream_handle(dev)))
         return peaks
 
     def autotune(self, t, y, offsets=None, cache_path=None, ablations=False, return_trials=False):
@@ -478,8 +506,12 @@ class Plan:
         also measure the trig/staging ablation kernels.  return_trials: return
         (config, [trial dicts]) with every measured candidate."""
         torch = _torch()
-        _require(t, "t", torch.float64)
-        _require(y, "y", _dtypes(self.opts), t.device)
+        _require(t, "t", torch.float64, numel=self.total_nt)
+        _require(y, "y", _dtypes(self.opts), t.device, numel=self.total_nt)
+        if offsets is not None:
+            _require(offsets, "offsets", torch.int64, t.device, numel=self.n_obj + 1)
+        elif self.n_obj > 1:
+            raise ValueError("a batch plan needs offsets")
         cp = cache_path.encode() if cache_path else None
         if not (ablations or return_trials):
             _check(lib().lsp_plan_autotune(self._h, _ptr(t), _ptr(y), _ptr(offsets), cp,

@@ -19,8 +19,8 @@ import time
 
 import numpy as np
 
-from . import FP32, Grid, MlpDims, NORM_STANDARD, PEAK_DTYPE, _check, _ptr, _stream_handle, batch, lib, \
-    peaks_to_numpy
+from . import FP32, Grid, MlpDims, NORM_STANDARD, PEAK_DTYPE, _check, _ptr, _require, _stream_handle, batch, \
+    lib, peaks_to_numpy
 
 FEAT_DIM = 512
 LAG_MAX = 16.0
@@ -35,6 +35,9 @@ def n_classes(n_f: int, stride: int = STRIDE) -> int:
 def featurize(t, y, offsets, grid: Grid, lag_max: float = LAG_MAX, want_f32: bool = False):
     """bfloat16 features (n_obj x 512) [and FP32 copy] of a CSR batch on the device."""
     import torch
+    _require(t, "t", torch.float64)
+    _require(y, "y", torch.float32, t.device, numel=t.numel())
+    _require(offsets, "offsets", torch.int64, t.device)
     n_obj = offsets.numel() - 1
     f16 = torch.empty((n_obj, FEAT_DIM), dtype=torch.bfloat16, device=t.device)
     f32 = torch.empty((n_obj, FEAT_DIM), dtype=torch.float32, device=t.device) if want_f32 else None
@@ -62,6 +65,9 @@ class Proposer:
                  k_windows: int = 8, stop_power: float = 0.5, fallback_power: float = 0.3,
                  inconclusive_fallback: bool = True):
         import torch
+        device = torch.device(device)
+        if device.type == "cuda" and device.index is None:
+            device = torch.device("cuda", torch.cuda.current_device())
         self.device = device
         self.n_f = int(n_f)
         self.dims = MlpDims(FEAT_DIM, hidden, n_hidden, n_classes(n_f))
@@ -100,8 +106,15 @@ class Proposer:
         return self._ws
 
     # -- network ------------------------------------------------------------
+    def _require_x(self, x16):
+        import torch
+        if x16.dim() != 2 or x16.shape[1] != self.dims.in_dim:
+            raise ValueError(f"x16 must be (batch, {self.dims.in_dim}), got {tuple(x16.shape)}")
+        _require(x16, "x16", torch.bfloat16, self.device)
+
     def forward(self, x16):
         import torch
+        self._require_x(x16)
         b = x16.shape[0]
         logits = torch.empty((b, self.dims.n_classes), dtype=torch.float32, device=self.device)
         ws = self._workspace(b)
@@ -111,7 +124,10 @@ class Proposer:
 
     def loss_grad(self, x16, labels):
         """Mean cross-entropy (device scalar) and the gradient (in self.grad)."""
+        import torch
+        self._require_x(x16)
         b = x16.shape[0]
+        _require(labels, "labels", torch.int32, self.device, numel=b)
         ws = self._workspace(b)
         _check(lib().lsp_mlp_loss_grad(ctypes.byref(self.dims), _ptr(self.params), _ptr(self.params16),
                                        _ptr(x16), _ptr(labels), b, _ptr(self._loss), _ptr(self.grad), _ptr(ws),
@@ -179,7 +195,11 @@ def refine(t, y, offsets, grid: Grid, classes, k_windows, stop_power, fallback_p
            inconclusive_fallback=True, window=WINDOW, stride=STRIDE, norm=NORM_STANDARD, workspace=None):
     """Windowed direct method with full-grid fallback; returns (peaks uint8 tensor, info int32)."""
     import torch
+    _require(t, "t", torch.float64)
+    _require(y, "y", torch.float32, t.device, numel=t.numel())
+    _require(offsets, "offsets", torch.int64, t.device)
     n_obj = offsets.numel() - 1
+    _require(classes, "classes", torch.int32, t.device, numel=n_obj * int(k_windows))
     n = ctypes.c_size_t()
     _check(lib().lsp_refine_workspace_size(n_obj, t.numel(), ctypes.byref(grid), ctypes.byref(n)))
     ws = workspace if workspace is not None else torch.empty(max(int(n.value), 256), dtype=torch.uint8,

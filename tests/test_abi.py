@@ -5,6 +5,7 @@ import ctypes
 import os
 import re
 
+import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -214,3 +215,31 @@ int main(void) {
         assert int(out["lsp_trial." + name]) == getattr(L.Trial, name).offset
     for name in ("power", "freq", "period", "flags"):
         assert int(out["lsp_peak." + name]) == L.PEAK_DTYPE.fields[name][1]
+
+
+def test_host_entry_point_checks_buffers_before_any_call(lsp_mod):
+    """execute_host hands raw host pointers to the library, which reads or
+    writes exactly the plan's sizes: wrong dtypes, lengths, or peaks records
+    are refused in Python first (no plan handle or GPU is touched)."""
+    import torch
+    lsp = lsp_mod
+    plan = object.__new__(lsp.Plan)
+    plan.opts = lsp.make_opts()
+    plan.grid = lsp.Grid(0.1, 1.0, 100)
+    plan.n_obj, plan.total_nt, plan._h = 3, 30, None
+    t, y = np.zeros(30), np.zeros(30, dtype=np.float32)
+    off = np.array([0, 10, 20, 30], dtype=np.int64)
+    dev = torch.device("cuda", 0)
+    bad_calls = [
+        dict(t=np.zeros(29), y=y, offsets=off),                                   # short t
+        dict(t=t, y=np.zeros(30), offsets=off),                                   # FP64 y for an FP32 plan
+        dict(t=t, y=y, offsets=off[:3]),                                          # short offsets
+        dict(t=t, y=y, offsets=None),                                             # batch without offsets
+        dict(t=t, y=y, offsets=off, power=np.zeros((3, 99), dtype=np.float32)),    # short power
+        dict(t=t, y=y, offsets=off, power=torch.zeros((3, 100), dtype=torch.float64)),  # wrong dtype
+        dict(t=t, y=y, offsets=off, peaks=np.empty(2, dtype=lsp.PEAK_DTYPE)),      # too few records
+        dict(t=t, y=y, offsets=off, peaks=torch.empty(3 * 40 - 1, dtype=torch.uint8)),
+    ]
+    for kw in bad_calls:
+        with pytest.raises((TypeError, ValueError)):
+            plan.execute_host(device=dev, **kw)
