@@ -9,8 +9,7 @@
 //   uint32   queue[4]                   persistent-kernel work counter
 //   ChunkBest best[n_obj * n_chunks]    first maximum of each frequency chunk
 //   ChunkCand cand[n_obj * n_chunks]    top-3 local maxima + edge bins (top_k > 1)
-//   partial  part[split * n_f]          split-N_t partial sums (single object; 4 per
-//                                       frequency, the generalized periodogram's 6 in slots of 8)
+//   partial  part[split * n_f]          split-N_t partial sums (single object)
 #pragma once
 
 #include <cstdint>
