@@ -271,7 +271,9 @@ lsp_status lsp_plan_execute(lsp_plan* plan, const double* t, const void* y, cons
  * kernels directly into power_out if it is page-locked host memory, and
  * otherwise computed into a device buffer and copied back.  Pinned host
  * memory gives the fastest copies.  The first call allocates the plan's
- * device staging buffers (later calls reuse them).
+ * device staging buffers (later calls reuse them).  On an error the call
+ * still waits for the copies it had enqueued, so the host buffers are free
+ * to reuse once it returns.
  */
 lsp_status lsp_plan_execute_host(lsp_plan* plan, const double* t, const void* y,
                                  const int64_t* offsets, void* power_out, lsp_peak* peaks,

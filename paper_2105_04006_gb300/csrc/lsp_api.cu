@@ -791,9 +791,9 @@ lsp_status lsp_plan_execute(lsp_plan* p, const double* t, const void* y, const i
   return LSP_OK;
 }
 
-lsp_status lsp_plan_execute_host(lsp_plan* p, const double* t, const void* y,
-                                 const int64_t* offsets, void* power_out, lsp_peak* peaks,
-                                 lsp_stream_t stream) {
+static lsp_status execute_host_impl(lsp_plan* p, const double* t, const void* y,
+                                    const int64_t* offsets, void* power_out, lsp_peak* peaks,
+                                    lsp_stream_t stream) {
   g_err.clear();
   if (!p) return fail(LSP_E_ARG, "plan is NULL");
   lsp_status st = check_io(p->total_nt, t, y);
@@ -862,6 +862,20 @@ lsp_status lsp_plan_execute_host(lsp_plan* p, const double* t, const void* y,
     LSP_CUDA(cudaMemcpyAsync(power_out, p->d_power, pbytes, cudaMemcpyDeviceToHost, s), "D2H power");
   LSP_CUDA(cudaStreamSynchronize(s), "synchronize");
   return LSP_OK;
+}
+
+lsp_status lsp_plan_execute_host(lsp_plan* p, const double* t, const void* y,
+                                 const int64_t* offsets, void* power_out, lsp_peak* peaks,
+                                 lsp_stream_t stream) {
+  const lsp_status st = execute_host_impl(p, t, y, offsets, power_out, peaks, stream);
+  if (st != LSP_OK && p) {
+    // copies enqueued before the failure may still read or write the caller's
+    // host buffers: let them end before the error is reported
+    cudaStreamSynchronize((cudaStream_t)stream);
+    if (p->copy_stream) cudaStreamSynchronize(p->copy_stream);
+    cudaGetLastError();
+  }
+  return st;
 }
 
 lsp_status lsp_plan_set_host_parts(lsp_plan* p, int32_t parts) {
