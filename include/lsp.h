@@ -307,8 +307,9 @@ lsp_status lsp_plan_get_host_parts(const lsp_plan* plan, int64_t power_bytes, in
 /*
  * Measure the candidate launch configurations on these inputs, keep the
  * fastest one whose powers stay within the FP32 error gate (1e-4 absolute
- * in P_n: the first object's periodogram against the FP64 path), and use it
- * from now on.  Synchronises `stream`.  When cache_path is not NULL the
+ * in P_n: the first object's periodogram against the FP64 path; skipped
+ * when that object has fewer than two observations or offsets outside the
+ * inputs), and use it from now on.  Synchronises `stream`.  When cache_path is not NULL the
  * choice is read from / appended to that JSON-lines file, keyed by device,
  * shape class and options.
  */

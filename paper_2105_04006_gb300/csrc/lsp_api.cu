@@ -968,7 +968,9 @@ lsp_status lsp_plan_autotune_ex(lsp_plan* p, const double* t, const void* y, con
     g_lo = h[0];
     g_n = h[1] - h[0];
   }
-  const bool gate = p->opts.precision == LSP_FP32 && g_n >= 2;
+  // (the probe object must lie inside the inputs: the kernels flag bad
+  // offsets, but the gate reads this object's magnitudes directly)
+  const bool gate = p->opts.precision == LSP_FP32 && g_n >= 2 && g_lo >= 0 && g_n <= p->total_nt - g_lo;
   double* ref = nullptr;   // FP64 periodogram of the probe object
   double* y64 = nullptr;
   float* pw = nullptr;
