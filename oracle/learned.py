@@ -22,6 +22,17 @@ shape (fan_in, fan_out), row-major.  Loss: mean softmax cross-entropy.
 ``bf16=True`` rounds to bfloat16 (nearest-even) exactly where the GPU
 kernels store bfloat16: inputs, weights, hidden activations, and the
 back-propagated gradients of the pre-activations.
+
+Refinement windows and the refine rule (this project's reading of the
+"top-k windows, refine, fall back" workload):
+  class c covers the ``window`` bins starting at c*stride + stride/2 - window/2,
+  moved inside the grid [0, n_f);
+  the proposed windows of an object are evaluated in rank order; each gives
+  the first maximum of the periodogram over its bins; the running best keeps
+  the larger power (the lower bin on a tie); evaluation stops once the best
+  power reaches stop_power or the windows run out;
+  the object falls back to the full grid when its best power is below
+  fallback_power or, with ``inconclusive``, when no window reached stop_power.
 """
 from __future__ import annotations
 
@@ -114,8 +125,14 @@ def forward(theta, x, shapes, bf16_mode=False):
     raise AssertionError
 
 
-def loss_and_grad(theta, x, labels, shapes, bf16_mode=False):
-    """Mean softmax cross-entropy and its gradient w.r.t. the flat parameters."""
+def loss_and_grad(theta, x, labels, shapes, bf16_mode=False, return_intermediates=False):
+    """Mean softmax cross-entropy and its gradient w.r.t. the flat parameters.
+
+    With ``return_intermediates`` a third value holds, per layer l, the layer's
+    input ``acts[l]``, its weights as used ``w[l]``, its pre-activation ``z[l]``
+    and the gradient of the loss with respect to ``z[l]`` as used ``dz[l]``
+    (rounded to bfloat16 in ``bf16_mode``, like the stored copies).
+    """
     rnd = bf16 if bf16_mode else (lambda v: np.asarray(v, dtype=np.float64))
     theta = np.asarray(theta, dtype=np.float64)
     params = unpack(theta, shapes)
@@ -130,15 +147,21 @@ def loss_and_grad(theta, x, labels, shapes, bf16_mode=False):
     dz[np.arange(bsz), lab] -= 1.0
     dz = rnd(dz / bsz)
     grads = [None] * len(params)
+    dzs = [None] * len(params)
     for l in range(len(params) - 1, -1, -1):
         w, _ = params[l]
         a_in = acts[l]
+        dzs[l] = dz
         grads[l] = (a_in.T @ dz, dz.sum(axis=0))
         if l > 0:
             da = dz @ rnd(w).T
             dz = rnd(da * (acts[l] > 0))
     flat = np.concatenate([np.concatenate([gw.ravel(), gb]) for gw, gb in grads])
-    return loss, flat
+    if not return_intermediates:
+        return loss, flat
+    zs = [acts[l] @ rnd(w) + b for l, (w, b) in enumerate(params)]
+    inter = dict(acts=acts, w=[rnd(w) for w, _ in params], z=zs, dz=dzs)
+    return loss, flat, inter
 
 
 def init_params(shapes, seed):
@@ -160,3 +183,45 @@ def adamw_step(theta, grad, m, v, step, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-
     vh = v / (1 - beta2 ** step)
     theta = theta - lr * (mh / (np.sqrt(vh) + eps) + wd * theta)
     return theta, m, v
+
+
+# ------------------------------------------------------- refine windows
+def window_start(c, n_f, window=2048, stride=1024):
+    """First bin of window class c: c*stride + stride/2 - window/2, moved inside [0, n_f)."""
+    s = int(c) * int(stride) + int(stride) // 2 - int(window) // 2
+    s = min(s, int(n_f) - int(window))
+    return max(s, 0)
+
+
+def window_bins(c, n_f, window=2048, stride=1024):
+    """Grid indices of window class c (at most n_f of them)."""
+    s = window_start(c, n_f, window, stride)
+    return np.arange(s, min(s + int(window), int(n_f)), dtype=np.int64)
+
+
+def first_max(power, bins):
+    """(power, bin) of the first maximum of ``power`` over ``bins`` (bins ascending)."""
+    p = np.asarray(power, dtype=np.float64)
+    i = int(np.argmax(p))  # numpy's argmax returns the first of equal maxima
+    return float(p[i]), int(bins[i])
+
+
+def refine_replay(window_maxima, stop_power, fallback_power, inconclusive=True):
+    """The refine rule over one object's ranked windows.
+
+    ``window_maxima`` lists, in rank order, the (power, bin) first maximum of
+    every proposed window (as if all were evaluated).  Returns rounds (windows
+    evaluated), stopped, fallback and the best (power, bin) of the evaluated
+    windows.
+    """
+    best_p, best_k = 0.0, -1
+    rounds, stopped = 0, False
+    for p, k in window_maxima:
+        rounds += 1
+        if k >= 0 and (p > best_p or (p == best_p and (best_k < 0 or k < best_k))):
+            best_p, best_k = float(p), int(k)
+        stopped = best_p >= stop_power
+        if stopped:
+            break
+    fallback = best_p < fallback_power or (bool(inconclusive) and not stopped)
+    return dict(rounds=rounds, stopped=stopped, fallback=fallback, best_p=best_p, best_k=best_k)
