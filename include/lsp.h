@@ -168,19 +168,30 @@ lsp_status lsp_batch(const double* t, const void* y, const int64_t* offsets, int
  * its own pool, a C caller without a device allocator).  The paper has no
  * counterpart: this is a deployment convenience of this library.
  * Arguments and results are those of lsp_batch; the scratch memory is a
- * fixed device array of LSP_NOALLOC_SCRATCH_BYTES inside the library, which
- * every GPU that loads the library holds until the process exits.  A shape
- * whose lsp_workspace_size exceeds it returns LSP_E_WORKSPACE, launching
- * nothing.  The call allocates nothing.  All calls share that one array:
- * calls that overlap on the GPU (different streams or unordered host
- * threads) race on it, so order them.  Each call clears what must start at
- * zero.  The first call on a device looks up the array's address with that
- * device current; make it outside any stream capture.
+ * fixed device array of LSP_NOALLOC_SCRATCH_BYTES inside the library.  A
+ * shape whose lsp_workspace_size exceeds it returns LSP_E_WORKSPACE,
+ * launching nothing; an empty batch returns LSP_OK at once.  The call
+ * allocates nothing itself.  The CUDA runtime reserves the array in a
+ * device's memory when it loads the library's module there -- with lazy
+ * module loading, at the first lsp_noalloc_prepare or lsp_batch_noalloc on
+ * that device -- and keeps it until the process exits; a caller that must
+ * not see that reservation later calls lsp_noalloc_prepare at start-up.  If
+ * the device has no room for it the call returns LSP_E_NOMEM.  All calls
+ * share the one array: calls that overlap on the GPU (different streams or
+ * unordered host threads) race on it, so order them.  Each call clears what
+ * must start at zero.  The array's address is looked up once per device,
+ * with that device current, in the runtime's primary context: make the
+ * first call outside any stream capture, and call lsp_noalloc_prepare again
+ * after cudaDeviceReset or when another context is current.
  */
 #define LSP_NOALLOC_SCRATCH_BYTES (32u << 20)
 lsp_status lsp_batch_noalloc(const double* t, const void* y, const int64_t* offsets, int64_t n_obj,
                              int64_t total_nt, const lsp_grid* grid, const lsp_opts* opts,
                              void* power_out, lsp_peak* peaks, lsp_stream_t stream);
+/* Reserves the scratch array of lsp_batch_noalloc on the current device (if
+ * not yet done) and looks its address up afresh.  LSP_E_NOMEM if the device
+ * has no room for it, LSP_E_CUDA for another runtime error. */
+lsp_status lsp_noalloc_prepare(void);
 
 /*
  * Generalized periodogram (Section 4.11: photometric errors, floating
@@ -402,7 +413,9 @@ lsp_status lsp_featurize(const double* t, const float* y, const int64_t* offsets
                          int64_t total_nt, const lsp_grid* grid, float lag_max, uint16_t* feat_bf16,
                          float* feat_f32, lsp_stream_t stream);
 
-/* Logits (batch x n_classes, FP32) of the MLP on bfloat16 inputs x (batch x in_dim). */
+/* Logits (batch x n_classes, FP32) of the MLP on bfloat16 inputs x (batch x in_dim);
+ * batch <= LSP_MLP_MAX_BATCH rows per call. */
+#define LSP_MLP_MAX_BATCH 4194240
 lsp_status lsp_mlp_forward(const lsp_mlp_dims* dims, const float* params, const uint16_t* params_bf16,
                            const uint16_t* x_bf16, int64_t batch, float* logits, void* workspace,
                            size_t ws_bytes, lsp_stream_t stream);
@@ -454,6 +467,58 @@ lsp_status lsp_refine_windows(const double* t, const float* y, const int64_t* of
                               int64_t stride, float stop_power, float fallback_power,
                               int32_t inconclusive_fallback, lsp_peak* peaks, int32_t* info,
                               void* workspace, size_t ws_bytes, lsp_stream_t stream);
+
+/*
+ * The learned path in one call: the 512 features of every light curve
+ * (lsp_featurize), the network's logits (lsp_mlp_forward), each object's
+ * k_windows best window classes (lsp_top_classes) and the ranked refine
+ * with its full-grid fallback (lsp_refine_windows), launched on `stream`
+ * with no host synchronisation.  The results equal those of the four calls
+ * made in that order, bit for bit.  Not in the paper: the proposal network
+ * and its windows are this library's learned stage (see above).
+ *
+ * The network is described by an lsp_proposer; its parameter arrays are the
+ * caller's device memory and are only read.  t, y, offsets, n_obj, total_nt
+ * and grid are as in lsp_batch (y float).  peaks (n_obj records) and info
+ * (n_obj words, nullable) are as in lsp_refine_windows; classes_out
+ * (nullable, n_obj x k_windows int32) receives the proposed classes, best
+ * first.  workspace must hold lsp_propose_refine_workspace_size bytes and be
+ * 256-byte aligned; it holds the features, the hidden activations, the
+ * logits, the classes and the refine's state.
+ * Errors: LSP_E_ARG for a bad proposer (in_dim not LSP_FEAT_DIM, k_windows
+ * outside 1..16 or above n_classes, lag_max <= 0, NULL parameters), bad
+ * window or stride, NULL arrays, or a small or misaligned workspace;
+ * LSP_E_CUDA if a launch fails.
+ */
+typedef struct lsp_proposer {
+  lsp_mlp_dims dims;             /* in_dim = LSP_FEAT_DIM; n_classes = window classes of the grid */
+  const float* params;           /* device: FP32 flat parameters (layout of lsp_mlp_forward) */
+  const uint16_t* params_bf16;   /* device: their bfloat16 copy */
+  int64_t window;                /* bins per refinement window, 1..2048 */
+  int64_t stride;                /* bins between window classes (class c centred on c*stride + stride/2) */
+  float lag_max;                 /* the featurizer's lag limit, in units of t */
+  int32_t k_windows;             /* proposals per object, 1..16 and at most n_classes */
+  float stop_power;              /* an object stops once its best refined power reaches this */
+  float fallback_power;          /* full grid when the best refined power is below this */
+  int32_t inconclusive_fallback; /* nonzero: full grid also when no window reached stop_power */
+  int32_t norm;                  /* lsp_norm of the thresholds and of the returned powers */
+} lsp_proposer; /* 72 bytes */
+
+lsp_status lsp_propose_refine_workspace_size(const lsp_proposer* net, int64_t n_obj, int64_t total_nt,
+                                             const lsp_grid* grid, size_t* bytes);
+lsp_status lsp_propose_refine(const lsp_proposer* net, const double* t, const float* y, const int64_t* offsets,
+                              int64_t n_obj, int64_t total_nt, const lsp_grid* grid, lsp_peak* peaks,
+                              int32_t* info, int32_t* classes_out, void* workspace, size_t ws_bytes,
+                              lsp_stream_t stream);
+
+/*
+ * Training labels of the learned stage: labels[o] = the window class of
+ * peaks[o].idx, i.e. idx / stride clamped to [0, n_classes - 1] (0 for an
+ * object without a peak).  peaks are device records from lsp_batch
+ * (top_k = 1).  Errors: LSP_E_ARG for stride < 1, n_classes < 1 or NULL arrays.
+ */
+lsp_status lsp_window_labels(const lsp_peak* peaks, int64_t n_obj, int64_t stride, int32_t n_classes,
+                             int32_t* labels, lsp_stream_t stream);
 
 /*
  * Calibration probe of the FMA pipes (no counterpart in the paper): runs

@@ -92,12 +92,21 @@ EXPORTS = [
     "lsp_mlp_loss_grad", "lsp_mlp_adamw", "lsp_to_bf16", "lsp_top_classes", "lsp_refine_workspace_size",
     "lsp_refine_windows", "lsp_batch_gls", "lsp_periodogram_gls", "lsp_workspace_size_gls",
     "lsp_probe_fma_rates", "lsp_plan_autotune_ex", "lsp_plan_set_host_parts", "lsp_plan_get_host_parts",
+    "lsp_propose_refine", "lsp_propose_refine_workspace_size", "lsp_window_labels", "lsp_noalloc_prepare",
 ]
 
 
 class MlpDims(ctypes.Structure):
     _fields_ = [("in_dim", ctypes.c_int32), ("hidden", ctypes.c_int32), ("n_hidden", ctypes.c_int32),
                 ("n_classes", ctypes.c_int32)]
+
+
+class Proposer(ctypes.Structure):
+    """lsp_proposer: the learned stage's network and refine settings."""
+    _fields_ = [("dims", MlpDims), ("params", ctypes.c_void_p), ("params_bf16", ctypes.c_void_p),
+                ("window", ctypes.c_int64), ("stride", ctypes.c_int64), ("lag_max", ctypes.c_float),
+                ("k_windows", ctypes.c_int32), ("stop_power", ctypes.c_float), ("fallback_power", ctypes.c_float),
+                ("inconclusive_fallback", ctypes.c_int32), ("norm", ctypes.c_int32)]
 
 
 def lib():
@@ -151,6 +160,11 @@ def lib():
             L.lsp_refine_workspace_size.argtypes = [i64, i64, GP, ctypes.POINTER(sz)]
             L.lsp_refine_windows.argtypes = [P, P, P, i64, i64, GP, i32, P, i32, i64, i64, f32, f32, i32, P,
                                              P, P, sz, P]
+            PP = ctypes.POINTER(Proposer)
+            L.lsp_propose_refine_workspace_size.argtypes = [PP, i64, i64, GP, ctypes.POINTER(sz)]
+            L.lsp_propose_refine.argtypes = [PP, P, P, P, i64, i64, GP, P, P, P, P, sz, P]
+            L.lsp_window_labels.argtypes = [P, i64, i64, i32, P, P]
+            L.lsp_noalloc_prepare.argtypes = []
             L.lsp_plan_destroy.argtypes = [P]
             L.lsp_plan_destroy.restype = None
             for name in EXPORTS:

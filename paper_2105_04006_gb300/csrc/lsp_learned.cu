@@ -406,6 +406,16 @@ __global__ void topk_kernel(const float* __restrict__ logits, int64_t rows, int 
   for (int i = 0; i < k; ++i) out[r * k + i] = tc[i];
 }
 
+// Window class of each object's full-grid first maximum: the training label.
+__global__ void labels_kernel(const lsp_peak* __restrict__ peaks, int64_t n_obj, int64_t stride, int n_cls,
+                              int32_t* __restrict__ labels) {
+  const int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (o >= n_obj) return;
+  const int64_t k = peaks[o].idx;
+  int64_t c = k > 0 ? k / stride : 0;
+  labels[o] = (int32_t)(c < n_cls ? c : n_cls - 1);
+}
+
 // ===================================================== refine + fallback
 // Per-object refinement state (in the workspace).
 struct RefineState {
@@ -659,6 +669,7 @@ lsp_status lsp_mlp_forward(const lsp_mlp_dims* dims, const float* params, const 
   lsp_status st = make_layers(dims, &L);
   if (st) return st;
   if (batch < 1 || !params || !params_bf16 || !x_bf16 || !logits) return err_arg("NULL argument");
+  if (batch > LSP_MLP_MAX_BATCH) return err_arg("batch exceeds LSP_MLP_MAX_BATCH rows");
   MlpWs w;
   mlp_ws_layout(L, batch, (char*)workspace, &w);
   if (!workspace || ws_bytes < w.total) return err_arg("MLP workspace too small");
@@ -675,6 +686,7 @@ lsp_status lsp_mlp_loss_grad(const lsp_mlp_dims* dims, const float* params, cons
   if (st) return st;
   if (batch < 1 || !params || !params_bf16 || !x_bf16 || !labels || !loss || !grad)
     return err_arg("NULL argument");
+  if (batch > LSP_MLP_MAX_BATCH) return err_arg("batch exceeds LSP_MLP_MAX_BATCH rows");
   MlpWs w;
   mlp_ws_layout(L, batch, (char*)workspace, &w);
   if (!workspace || ws_bytes < w.total) return err_arg("MLP workspace too small");
@@ -733,7 +745,10 @@ lsp_status lsp_mlp_adamw(int64_t n, float* params, uint16_t* params_bf16, const 
                          float* v, int64_t step, float lr, float beta1, float beta2, float eps,
                          float weight_decay, lsp_stream_t stream) {
   if (n < 1 || !params || !params_bf16 || !grad || !m || !v || step < 1) return err_arg("bad argument");
-  const float bc1 = 1.0f - powf(beta1, (float)step), bc2 = 1.0f - powf(beta2, (float)step);
+  // bias corrections 1 - beta^step in FP64, rounded once: in FP32 the
+  // subtraction cancels (1 - 0.999^2 keeps only a few correct bits)
+  const float bc1 = (float)(1.0 - pow((double)beta1, (double)step));
+  const float bc2 = (float)(1.0 - pow((double)beta2, (double)step));
   adamw_kernel<<<1024, 256, 0, (cudaStream_t)stream>>>(n, params, (bf16*)params_bf16, grad, m, v, lr, beta1,
                                                        beta2, eps, weight_decay, bc1, bc2);
   LEARN_CUDA(cudaGetLastError(), "AdamW");
@@ -806,26 +821,33 @@ lsp_status lsp_refine_workspace_size(int64_t n_obj, int64_t total_nt, const lsp_
   return LSP_OK;
 }
 
-lsp_status lsp_refine_windows(const double* t, const float* y, const int64_t* offsets, int64_t n_obj,
-                              int64_t total_nt, const lsp_grid* grid, int32_t norm, const int32_t* classes,
-                              int32_t k_windows, int64_t window, int64_t stride, float stop_power,
-                              float fallback_power, int32_t inconclusive_fallback, lsp_peak* peaks,
-                              int32_t* info, void* workspace, size_t ws_bytes, lsp_stream_t stream) {
+}  // extern "C"
+
+namespace {
+
+lsp_status check_refine_args(const double* t, const float* y, const int64_t* offsets, int64_t n_obj,
+                             int64_t total_nt, const lsp_grid* grid, const int32_t* classes, int32_t k_windows,
+                             int64_t window, int64_t stride, const lsp_peak* peaks) {
   if (!grid || !(grid->f_min > 0.0) || !(grid->f_max > grid->f_min) || grid->n_f < 1)
     return err_arg("bad grid");
   if (n_obj < 0 || n_obj > INT32_MAX || total_nt < 0) return err_arg("bad n_obj or total_nt");
   if (n_obj == 0) return LSP_OK;
-  if (!t || !y || !offsets || !classes || !peaks) return err_arg("NULL argument");
+  if (!t || !y || !offsets || !peaks) return err_arg("NULL argument");
+  if (!classes) return err_arg("classes is NULL");
   if (k_windows < 1 || k_windows > 64) return err_arg("k_windows must be 1..64");
   const int64_t chunk = (int64_t)kRefineThreads * 2 * kRefineK;
   if (window < 1 || window > chunk) return err_arg("window must be 1..2048");
   if (stride < 1) return err_arg("stride must be >= 1");
-  RefineLayout r;
-  refine_layout(n_obj, total_nt, grid->n_f, &r);
-  if (!workspace || ws_bytes < r.total || ((uintptr_t)workspace) % 256)
-    return err_arg("refine workspace too small or misaligned");
-  cudaStream_t s = (cudaStream_t)stream;
-  char* ws = (char*)workspace;
+  return LSP_OK;
+}
+
+// The windowed refine and the full-grid fallback on a laid-out workspace
+// (arguments already checked).
+lsp_status refine_impl(const double* t, const float* y, const int64_t* offsets, int64_t n_obj, int64_t total_nt,
+                       const lsp_grid* grid, int32_t norm, const int32_t* classes, int32_t k_windows,
+                       int64_t window, int64_t stride, float stop_power, float fallback_power,
+                       int32_t inconclusive_fallback, lsp_peak* peaks, int32_t* info, char* ws,
+                       const RefineLayout& r, cudaStream_t s) {
   ObjInfo* obj = (ObjInfo*)(ws + r.off_obj);
   RecF32* rec = (RecF32*)(ws + r.off_rec);
   RefineState* state = (RefineState*)(ws + r.off_state);
@@ -892,6 +914,146 @@ lsp_status lsp_refine_windows(const double* t, const float* y, const int64_t* of
                                      r.n_chunks, grid->f_min, df, peaks, info);
   LEARN_CUDA(cudaGetLastError(), "refine finalize");
   return LSP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+lsp_status lsp_refine_windows(const double* t, const float* y, const int64_t* offsets, int64_t n_obj,
+                              int64_t total_nt, const lsp_grid* grid, int32_t norm, const int32_t* classes,
+                              int32_t k_windows, int64_t window, int64_t stride, float stop_power,
+                              float fallback_power, int32_t inconclusive_fallback, lsp_peak* peaks,
+                              int32_t* info, void* workspace, size_t ws_bytes, lsp_stream_t stream) {
+  lsp_status st = check_refine_args(t, y, offsets, n_obj, total_nt, grid, classes, k_windows, window, stride,
+                                    peaks);
+  if (st || n_obj == 0) return st;
+  RefineLayout r;
+  refine_layout(n_obj, total_nt, grid->n_f, &r);
+  if (!workspace || ws_bytes < r.total || ((uintptr_t)workspace) % 256)
+    return err_arg("refine workspace too small or misaligned");
+  return refine_impl(t, y, offsets, n_obj, total_nt, grid, norm, classes, k_windows, window, stride, stop_power,
+                     fallback_power, inconclusive_fallback, peaks, info, (char*)workspace, r,
+                     (cudaStream_t)stream);
+}
+
+}  // extern "C"
+
+// ============================================== the learned path in one call
+namespace {
+
+// The network runs on passes of at most kProposeRows objects, which bounds
+// its scratch and keeps each GEMM's grid within its limits.
+constexpr int64_t kProposeRows = (int64_t)1 << 20;
+
+struct ProposeLayout {
+  size_t off_feat, off_act[2], off_logits, off_cls, off_refine, total;
+  RefineLayout r;
+};
+
+void propose_layout(const Layers& L, int64_t n_obj, int64_t total_nt, int64_t n_f, int k_windows,
+                    ProposeLayout* p) {
+  size_t off = 0;
+  auto take = [&](size_t b) {
+    size_t at = off;
+    off = align256(off + b);
+    return at;
+  };
+  p->off_feat = take((size_t)n_obj * LSP_FEAT_DIM * sizeof(bf16));
+  int maxw = 0;
+  for (int l = 0; l + 1 < L.n; ++l) maxw = L.out[l] > maxw ? L.out[l] : maxw;
+  const int64_t rows = n_obj < kProposeRows ? n_obj : kProposeRows;
+  for (int i = 0; i < 2; ++i) p->off_act[i] = take((size_t)rows * maxw * sizeof(bf16));
+  p->off_logits = take((size_t)rows * L.out[L.n - 1] * sizeof(float));
+  p->off_cls = take((size_t)n_obj * k_windows * sizeof(int32_t));
+  refine_layout(n_obj, total_nt, n_f, &p->r);
+  p->off_refine = take(p->r.total);
+  p->total = off;
+}
+
+lsp_status check_proposer(const lsp_proposer* net, Layers* L) {
+  if (!net) return err_arg("proposer is NULL");
+  lsp_status st = make_layers(&net->dims, L);
+  if (st) return st;
+  if (net->dims.in_dim != LSP_FEAT_DIM) return err_arg("the proposer's in_dim must be LSP_FEAT_DIM");
+  if (!net->params || !net->params_bf16) return err_arg("the proposer's parameters are NULL");
+  if (net->k_windows < 1 || net->k_windows > 16 || net->k_windows > net->dims.n_classes)
+    return err_arg("k_windows must be 1..16 and at most n_classes");
+  if (!(net->lag_max > 0.0f)) return err_arg("lag_max must be > 0");
+  if (net->norm != LSP_NORM_PSD && net->norm != LSP_NORM_STANDARD) return err_arg("bad norm");
+  return LSP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+lsp_status lsp_window_labels(const lsp_peak* peaks, int64_t n_obj, int64_t stride, int32_t n_classes,
+                             int32_t* labels, lsp_stream_t stream) {
+  if (n_obj < 0 || stride < 1 || n_classes < 1) return err_arg("bad n_obj, stride or n_classes");
+  if (n_obj == 0) return LSP_OK;
+  if (!peaks || !labels) return err_arg("NULL argument");
+  labels_kernel<<<(unsigned)((n_obj + 255) / 256), 256, 0, (cudaStream_t)stream>>>(peaks, n_obj, stride,
+                                                                                   n_classes, labels);
+  LEARN_CUDA(cudaGetLastError(), "window labels");
+  return LSP_OK;
+}
+
+lsp_status lsp_propose_refine_workspace_size(const lsp_proposer* net, int64_t n_obj, int64_t total_nt,
+                                             const lsp_grid* grid, size_t* bytes) {
+  if (!bytes || !grid || n_obj < 0 || total_nt < 0 || grid->n_f < 1) return err_arg("bad argument");
+  Layers L;
+  lsp_status st = check_proposer(net, &L);
+  if (st) return st;
+  ProposeLayout p;
+  propose_layout(L, n_obj, total_nt, grid->n_f, net->k_windows, &p);
+  *bytes = p.total;
+  return LSP_OK;
+}
+
+lsp_status lsp_propose_refine(const lsp_proposer* net, const double* t, const float* y, const int64_t* offsets,
+                              int64_t n_obj, int64_t total_nt, const lsp_grid* grid, lsp_peak* peaks,
+                              int32_t* info, int32_t* classes_out, void* workspace, size_t ws_bytes,
+                              lsp_stream_t stream) {
+  Layers L;
+  lsp_status st = check_proposer(net, &L);
+  if (st) return st;
+  // the classes pointer is checked once it exists (inside the workspace)
+  int32_t dummy = 0;
+  st = check_refine_args(t, y, offsets, n_obj, total_nt, grid, &dummy, net->k_windows, net->window, net->stride,
+                         peaks);
+  if (st || n_obj == 0) return st;
+  ProposeLayout p;
+  propose_layout(L, n_obj, total_nt, grid->n_f, net->k_windows, &p);
+  if (!workspace || ws_bytes < p.total || ((uintptr_t)workspace) % 256)
+    return err_arg("propose-refine workspace too small or misaligned");
+  cudaStream_t s = (cudaStream_t)stream;
+  char* ws = (char*)workspace;
+  bf16* feat = (bf16*)(ws + p.off_feat);
+  int32_t* cls = classes_out ? classes_out : (int32_t*)(ws + p.off_cls);
+  // 1. features
+  featurize_kernel<<<(unsigned)n_obj, kFeatThreads, 0, s>>>(t, y, offsets, total_nt, grid->f_min, grid->f_max,
+                                                             net->lag_max, feat, nullptr);
+  LEARN_CUDA(cudaGetLastError(), "featurize");
+  // 2. logits (hidden activations alternate between two buffers) and
+  // 3. the k best window classes per object, a pass of rows at a time
+  MlpWs w;
+  memset(&w, 0, sizeof w);
+  for (int l = 0; l + 1 < L.n; ++l) w.act[l] = (bf16*)(ws + p.off_act[l & 1]);
+  w.logits = (float*)(ws + p.off_logits);
+  for (int64_t r0 = 0; r0 < n_obj; r0 += kProposeRows) {
+    const int64_t rows = n_obj - r0 < kProposeRows ? n_obj - r0 : kProposeRows;
+    if ((st = mlp_forward_impl(L, net->params, (const bf16*)net->params_bf16, feat + r0 * LSP_FEAT_DIM, rows, w,
+                               s)))
+      return st;
+    topk_kernel<<<(unsigned)((rows + 127) / 128), 128, 0, s>>>(w.logits, rows, L.out[L.n - 1], net->k_windows,
+                                                                cls + r0 * net->k_windows);
+    LEARN_CUDA(cudaGetLastError(), "top classes");
+  }
+  // 4. refine in rank order, full grid where the refined peak is weak
+  return refine_impl(t, y, offsets, n_obj, total_nt, grid, net->norm, cls, net->k_windows, net->window,
+                     net->stride, net->stop_power, net->fallback_power, net->inconclusive_fallback, peaks, info,
+                     ws + p.off_refine, p.r, s);
 }
 
 }  // extern "C"

@@ -21,11 +21,13 @@ import numpy as np
 
 from . import FP32, Grid, MlpDims, NORM_STANDARD, PEAK_DTYPE, _check, _ptr, _require, _stream_handle, batch, \
     lib, peaks_to_numpy
+from . import Proposer as _ProposerStruct
 
 FEAT_DIM = 512
 LAG_MAX = 16.0
 WINDOW = 2048
 STRIDE = 1024
+REFINE_FALLBACK = 256  # bit of the refine's info word (LSP_REFINE_FALLBACK)
 
 
 def n_classes(n_f: int, stride: int = STRIDE) -> int:
@@ -152,6 +154,12 @@ class Proposer:
                                      _stream_handle(self.device)))
         return cls
 
+    def as_struct(self, window=WINDOW, stride=STRIDE, lag_max=LAG_MAX, norm=NORM_STANDARD):
+        """The lsp_proposer record of this network (pointers into its device tensors)."""
+        return _ProposerStruct(self.dims, self.params.data_ptr(), self.params16.data_ptr(), int(window),
+                               int(stride), float(lag_max), int(self.k_windows), float(self.stop_power),
+                               float(self.fallback_power), int(bool(self.inconclusive_fallback)), int(norm))
+
     # -- checkpoints --------------------------------------------------------
     def state_dict(self):
         return {"params": self.params.detach().cpu(), "m": self.m.detach().cpu(), "v": self.v.detach().cpu(),
@@ -180,6 +188,35 @@ class Proposer:
         if extra:
             sd["extra"] = extra
         torch.save(sd, path)
+
+    def save_npz(self, path, **meta):
+        """The network alone (FP32 parameters and settings, no optimizer state)
+        as a compressed numpy archive; `meta` adds string or number fields."""
+        d = dict(params=self.params.detach().cpu().numpy().astype(np.float32),
+                 dims=np.array([self.dims.in_dim, self.dims.hidden, self.dims.n_hidden, self.dims.n_classes]),
+                 n_f=np.array(self.n_f), k_windows=np.array(self.k_windows),
+                 stop_power=np.array(self.stop_power), fallback_power=np.array(self.fallback_power),
+                 inconclusive_fallback=np.array(int(bool(self.inconclusive_fallback))), step=np.array(self.step))
+        for k, v in meta.items():
+            d["meta_" + k] = np.array(v)
+        np.savez_compressed(path, **d)
+
+    @classmethod
+    def load_npz(cls, path, device):
+        """A network written by save_npz; returns (proposer, metadata dict)."""
+        import torch
+        with np.load(path) as z:
+            dims = [int(v) for v in z["dims"]]
+            p = cls(int(z["n_f"]), device, hidden=dims[1], n_hidden=dims[2], k_windows=int(z["k_windows"]),
+                    stop_power=float(z["stop_power"]), fallback_power=float(z["fallback_power"]),
+                    inconclusive_fallback=bool(int(z["inconclusive_fallback"])))
+            if dims != [p.dims.in_dim, p.dims.hidden, p.dims.n_hidden, p.dims.n_classes]:
+                raise ValueError(f"checkpoint dims {dims} do not match")
+            p.params.copy_(torch.from_numpy(z["params"]).to(p.device))
+            p.step = int(z["step"])
+            meta = {k[5:]: z[k].item() for k in z.files if k.startswith("meta_")}
+        p.refresh_bf16()
+        return p, meta
 
     @classmethod
     def load(cls, path, device):
@@ -214,12 +251,50 @@ def refine(t, y, offsets, grid: Grid, classes, k_windows, stop_power, fallback_p
     return peaks, info
 
 
+class LearnedPath:
+    """The learned path as one library call (lsp_propose_refine) on a CSR batch
+    on the device, with its workspace kept between calls of the same shape."""
+
+    def __init__(self, proposer: Proposer):
+        self.proposer = proposer
+        self._ws = None
+
+    def __call__(self, t, y, offsets, grid: Grid, classes_out=None):
+        """(peaks uint8 tensor of n_obj records, info int32 tensor)."""
+        import torch
+        _require(t, "t", torch.float64)
+        _require(y, "y", torch.float32, t.device, numel=t.numel())
+        _require(offsets, "offsets", torch.int64, t.device)
+        n_obj = offsets.numel() - 1
+        net = self.proposer.as_struct()
+        n = ctypes.c_size_t()
+        _check(lib().lsp_propose_refine_workspace_size(ctypes.byref(net), n_obj, t.numel(), ctypes.byref(grid),
+                                                       ctypes.byref(n)))
+        if self._ws is None or self._ws.numel() < int(n.value) or self._ws.device != t.device:
+            self._ws = torch.empty(max(int(n.value), 256), dtype=torch.uint8, device=t.device)
+        if classes_out is not None:
+            _require(classes_out, "classes_out", torch.int32, t.device, numel=n_obj * net.k_windows)
+        peaks = torch.empty(n_obj * 40, dtype=torch.uint8, device=t.device)
+        info = torch.empty(n_obj, dtype=torch.int32, device=t.device)
+        _check(lib().lsp_propose_refine(ctypes.byref(net), _ptr(t), _ptr(y), _ptr(offsets), n_obj, t.numel(),
+                                        ctypes.byref(grid), _ptr(peaks), _ptr(info), _ptr(classes_out),
+                                        _ptr(self._ws), self._ws.numel(), _stream_handle(t.device)))
+        return peaks, info
+
+
 def propose_and_refine(proposer: Proposer, t, y, offsets, grid: Grid):
-    """The whole learned path for a CSR batch on the device: (peaks, info)."""
-    x16 = featurize(t, y, offsets, grid)
-    cls = proposer.propose(x16)
-    return refine(t, y, offsets, grid, cls, proposer.k_windows, proposer.stop_power, proposer.fallback_power,
-                  proposer.inconclusive_fallback)
+    """The whole learned path for a CSR batch on the device, one library call: (peaks, info)."""
+    return LearnedPath(proposer)(t, y, offsets, grid)
+
+
+def window_labels(peaks, n_obj, n_cls, stride=STRIDE):
+    """Training labels: the window class of each object's full-grid first maximum."""
+    import torch
+    _require(peaks, "peaks", torch.uint8, numel=n_obj * 40)
+    labels = torch.empty(n_obj, dtype=torch.int32, device=peaks.device)
+    _check(lib().lsp_window_labels(_ptr(peaks), n_obj, int(stride), int(n_cls), _ptr(labels),
+                                   _stream_handle(peaks.device)))
+    return labels
 
 
 # --------------------------------------------------------------- training data
@@ -238,7 +313,7 @@ def labelled_set(n_obj, device, which="learned_train", part=0, grid=None):
     off = torch.tensor(b.offsets, dtype=torch.int64, device=device)
     _, peaks = batch(t, y, off, g)
     idx = torch.from_numpy(peaks_to_numpy(peaks)["idx"].copy()).to(device)
-    labels = torch.clamp(idx // STRIDE, min=0).to(torch.int32)
+    labels = window_labels(peaks, b.n_obj, n_classes(g.n_f))
     x16 = featurize(t, y, off, g)
     return dict(batch=b, grid=g, t=t, y=y, off=off, x16=x16, labels=labels, full_idx=idx)
 

@@ -175,6 +175,22 @@ def test_newer_entry_points_validate_without_launch(lsp_mod):
     assert L.lsp_refine_windows(P(256), P(512), P(768), 3, 100, ctypes.byref(g), 1, P(1024), 8, 2048, 1024,
                                 ctypes.c_float(0.5), ctypes.c_float(0.3), 1, P(2048), None, P(4096), 16,
                                 None) == 1  # workspace too small
+    # the learned path in one call: proposer and workspace checks
+    net = lsp_mod.Proposer(dims, 256, 512, 2048, 1024, 16.0, 8, 0.5, 0.3, 1, 1)
+    n = ctypes.c_size_t()
+    assert L.lsp_propose_refine_workspace_size(ctypes.byref(net), 3, 100, ctypes.byref(g), ctypes.byref(n)) == 0
+    assert n.value % 256 == 0 and n.value >= 3 * 512 * 2
+    args = (P(256), P(512), P(768), 3, 100, ctypes.byref(g), P(2048), None, None)
+    assert L.lsp_propose_refine(ctypes.byref(net), *args, P(4096), 16, None) == 1  # workspace too small
+    for field, value in (("k_windows", 17), ("lag_max", 0.0), ("params", None), ("window", 4096), ("stride", 0)):
+        bad_net = lsp_mod.Proposer.from_buffer_copy(net)
+        setattr(bad_net, field, value)
+        assert L.lsp_propose_refine(ctypes.byref(bad_net), *args, P(4096), 1 << 30, None) == 1, field
+    bad_net = lsp_mod.Proposer.from_buffer_copy(net)
+    bad_net.dims = lsp_mod.MlpDims(256, 256, 3, 98)
+    assert L.lsp_propose_refine(ctypes.byref(bad_net), *args, P(4096), 1 << 30, None) == 1
+    assert b"LSP_FEAT_DIM" in L.lsp_last_error()
+    assert L.lsp_window_labels(P(256), 3, 0, 98, P(512), None) == 1  # stride must be >= 1
     # grid rule
     assert lsp_mod.grid_for_span(0.24, 12.0, 3650.0).n_f == round((12.0 - 0.24) / (0.1 / 3650.0))
 
@@ -192,6 +208,10 @@ int main(void) {
   printf("lsp_grid %zu\\nlsp_opts %zu\\nlsp_peak %zu\\nlsp_config %zu\\nlsp_trial %zu\\nlsp_mlp_dims %zu\\n",
          sizeof(lsp_grid), sizeof(lsp_opts), sizeof(lsp_peak), sizeof(lsp_config), sizeof(lsp_trial),
          sizeof(lsp_mlp_dims));
+  printf("lsp_proposer %zu\\n", sizeof(lsp_proposer));
+  F(lsp_proposer, params); F(lsp_proposer, params_bf16); F(lsp_proposer, window); F(lsp_proposer, stride);
+  F(lsp_proposer, lag_max); F(lsp_proposer, k_windows); F(lsp_proposer, stop_power);
+  F(lsp_proposer, fallback_power); F(lsp_proposer, inconclusive_fallback); F(lsp_proposer, norm);
   F(lsp_config, packed); F(lsp_config, trig); F(lsp_config, staging);
   F(lsp_trial, ms); F(lsp_trial, max_err); F(lsp_trial, passed);
   F(lsp_peak, power); F(lsp_peak, freq); F(lsp_peak, period); F(lsp_peak, flags);
@@ -209,6 +229,10 @@ int main(void) {
     assert int(out["lsp_trial"]) == ctypes.sizeof(L.Trial)
     assert int(out["lsp_mlp_dims"]) == ctypes.sizeof(L.MlpDims)
     assert int(out["lsp_peak"]) == L.PEAK_DTYPE.itemsize
+    assert int(out["lsp_proposer"]) == ctypes.sizeof(L.Proposer) == 72
+    for name in ("params", "params_bf16", "window", "stride", "lag_max", "k_windows", "stop_power",
+                 "fallback_power", "inconclusive_fallback", "norm"):
+        assert int(out["lsp_proposer." + name]) == getattr(L.Proposer, name).offset, name
     for name in ("packed", "trig", "staging"):
         assert int(out["lsp_config." + name]) == getattr(L.Config, name).offset
     for name in ("ms", "max_err", "passed"):

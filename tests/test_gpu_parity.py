@@ -177,14 +177,12 @@ def test_batch_top3(env, small_batch, precision):
     tol = TOL32 if precision == "fp32" else TOL64
     for o in range(b.n_obj):
         pr = ref[precision]["power"][o]
-        for r in range(3):
-            kg, ko = int(pk["idx"][o, r]), int(ref[precision]["top_idx"][o, r])
-            if precision == "fp64":
-                assert kg == ko, (o, r, kg, ko)
-            elif abs(kg - ko) > 1:
-                # near-tie of two local maxima: the GPU's choice must be as high
-                assert abs(pr[kg] - pr[ko]) <= 2 * tol, (o, r, kg, ko)
-            assert abs(pk["power"][o, r] - ref[precision]["top_pow"][o, r]) <= tol * 2
+        if precision == "fp64":
+            for r in range(3):
+                assert int(pk["idx"][o, r]) == int(ref["fp64"]["top_idx"][o, r]), (o, r)
+                assert abs(pk["power"][o, r] - ref["fp64"]["top_pow"][o, r]) <= tol
+        else:
+            _check_top3(pk["idx"][o], pk["power"][o], pr, ref["fp32"]["top_idx"][o], ref["fp32"]["top_pow"][o], o)
 
 
 def test_batch_top3_every_variant(env, small_batch):
@@ -195,8 +193,8 @@ def test_batch_top3_every_variant(env, small_batch):
         _, pk = batch(env, b, "fp32", top_k=3, **var)
         pk = pk.reshape(b.n_obj, 3)
         for o in range(b.n_obj):
-            for r in range(3):
-                assert abs(pk["power"][o, r] - ref["fp32"]["top_pow"][o, r]) <= 2 * TOL32, (var, o, r)
+            _check_top3(pk["idx"][o], pk["power"][o], ref["fp32"]["power"][o], ref["fp32"]["top_idx"][o],
+                        ref["fp32"]["top_pow"][o], (str(var), o))
 
 
 def test_fused_argmax_matches_own_power(env, small_batch):
@@ -397,21 +395,53 @@ def test_full_single_small(env):
         assert_argmax_close(pk["idx"][0], np.argmax(ref), ref, tol)
 
 
+def _argmax_rates(pk_idx, pk_pow, b, objs, ref):
+    """Strict (|dk| <= 1) and tie-aware rates of the GPU's first maxima against
+    the oracle's on `objs`; tie-aware: a farther bin passes when the oracle's
+    own power there is within 1e-4 of its maximum.  Also the largest peak-power
+    error (GPU power against the oracle's at the GPU's bin)."""
+    strict, tie, worst = 0, 0, 0.0
+    g = b.grid
+    y = b.y.astype(np.float32).astype(np.float64)
+    for i, o in enumerate(objs):
+        kg, ko = int(pk_idx[o]), int(ref["arg_idx"][i])
+        if abs(kg - ko) <= 1:
+            strict += 1
+            tie += 1
+            if kg == ko:
+                worst = max(worst, abs(pk_pow[o] - ref["arg_pow"][i]))
+                continue
+        sl = slice(b.offsets[o], b.offsets[o + 1])
+        p, _ = oracle.lsp_single(b.t[sl], y[sl], g.f_min, g.f_max, g.n_f, k_sel=[kg])
+        worst = max(worst, abs(pk_pow[o] - p[0]))
+        if abs(kg - ko) > 1 and p[0] >= ref["arg_pow"][i] - TOL32:
+            tie += 1
+    n = len(objs)
+    return strict / n, tie / n, worst
+
+
 def test_full_ragged_survey_sampled(env):
-    """10000 objects, N_t in [50, 500], N_f=1e5, argmax only (the benchmark's launch)."""
+    """10000 objects, N_t in [50, 500], N_f=1e5, argmax only (the benchmark's
+    launch).  The FP32 first maxima against the FP64 oracle on 1000 objects
+    evenly spaced over the batch: at least 99.9 % within one bin, all of them
+    tie-aware, peak powers within 1e-4.  Over the whole batch, against the
+    FP64 GPU path (itself within 1e-10 of the oracle in the other tests): the
+    same 99.9 % and 1e-4."""
+    lsp, torch, dev = env
     b = synth.ragged_survey()
     _, pk = batch(env, b, "fp32")
     assert (pk["flags"] == 0).all()
-    sample = np.arange(0, b.n_obj, b.n_obj // 24)[:24]
-    sb = b.subset(sample)
-    ref = oracle_batch(sb, "fp32", return_power=True)
-    within = 0
-    for i, o in enumerate(sample):
-        assert abs(pk["power"][o] - ref["arg_pow"][i]) <= TOL32
-        within += abs(int(pk["idx"][o]) - int(ref["arg_idx"][i])) <= 1
-        assert_argmax_close(pk["idx"][o], ref["arg_idx"][i], ref["power"][i])
-    assert within >= len(sample) - 0  # >= 99.9% of the sample
+    sample = np.linspace(0, b.n_obj - 1, 1000).astype(np.int64)
+    ref = oracle_batch(b.subset(sample), "fp32")
+    strict, tie, worst = _argmax_rates(pk["idx"], pk["power"], b, sample, ref)
+    assert strict >= 0.999 and tie == 1.0, (strict, tie)
+    assert worst <= TOL32, worst
     assert (pk["power"] >= 0).all() and (pk["power"] <= 1.0 + 1e-5).all()
+    _, pk64 = batch(env, b, "fp64")
+    dk = np.abs(pk["idx"] - pk64["idx"])
+    assert np.mean(dk <= 1) >= 0.999, np.mean(dk <= 1)
+    same = dk == 0
+    assert np.max(np.abs(pk["power"][same] - pk64["power"][same])) <= TOL32
 
 
 def test_full_single_large_sampled(env):
@@ -431,21 +461,41 @@ def test_full_single_large_sampled(env):
         assert abs(k_top - (b.f_true[0] - b.grid.f_min) / b.grid.df) <= 1.0
 
 
+def _check_top3(pk_idx, pk_pow, pr, top_idx, top_pow, what):
+    """Top-3 local maxima against the oracle's: where the bins agree the powers
+    agree within 1e-4; the GPU's power at its own bin is always within 1e-4 of
+    the oracle's there; a different bin is allowed only for a near-tie of two
+    local maxima, i.e. oracle powers within the two FP32 errors (2e-4)."""
+    for r in range(3):
+        kg, ko = int(pk_idx[r]), int(top_idx[r])
+        assert abs(pk_pow[r] - pr[kg]) <= TOL32, (what, r, kg)
+        if kg == ko:
+            assert abs(pk_pow[r] - top_pow[r]) <= TOL32, (what, r)
+        else:
+            assert abs(pr[kg] - pr[ko]) <= 2 * TOL32, (what, r, kg, ko)
+
+
 def test_full_ragged_lognormal_top3_sampled(env):
-    """100000 objects, N_t log-uniform in [10, 2000], N_f=5e4, argmax + top-3."""
+    """100000 objects, N_t log-uniform in [10, 2000], N_f=5e4, argmax + top-3.
+    300 objects against the FP64 oracle: 200 evenly spaced and the 100 with
+    the most observations (N_t near 2000).  First maxima: at least 99.9 %
+    within one bin, all tie-aware; top-3 as in _check_top3."""
     b = synth.ragged_lognormal()
     _, pk = batch(env, b, "fp32", top_k=3)
     pk = pk.reshape(b.n_obj, 3)
-    sample = np.arange(0, b.n_obj, b.n_obj // 8)[:8]
+    longest = np.argsort(b.n_t, kind="stable")[-100:]
+    sample = np.unique(np.concatenate([np.linspace(0, b.n_obj - 1, 200).astype(np.int64), longest]))
+    assert sample.size >= 290 and b.n_t[sample].max() >= 1990
     sb = b.subset(sample)
     ref = oracle_batch(sb, "fp32", top_k=3, return_power=True)
+    strict = 0
     for i, o in enumerate(sample):
         pr = ref["power"][i]
-        for r in range(3):
-            kg, ko = int(pk["idx"][o, r]), int(ref["top_idx"][i, r])
-            if abs(kg - ko) > 1:
-                assert abs(pr[kg] - pr[ko]) <= 2 * TOL32, (o, r, kg, ko)
-            assert abs(pk["power"][o, r] - ref["top_pow"][i, r]) <= 2 * TOL32
+        kg, ko = int(pk["idx"][o, 0]), int(ref["arg_idx"][i])
+        strict += abs(kg - ko) <= 1
+        assert abs(kg - ko) <= 1 or pr[kg] >= pr[ko] - TOL32, (o, kg, ko)
+        _check_top3(pk["idx"][o], pk["power"][o], pr, ref["top_idx"][i], ref["top_pow"][i], int(o))
+    assert strict / sample.size >= 0.999, strict / sample.size
 
 
 def test_periodogram_written_to_pinned_host_memory(env, small_batch):
