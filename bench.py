@@ -3,18 +3,24 @@
 
 A step is one pass of the whole path over one batch resident in HBM: the
 prologue (centring, phase records), the work-queue order, the persistent
-trig-sum kernel with its fused power/argmax epilogue and the finalize
-kernel, replayed as one CUDA graph (``lsp_plan_execute``).  The default
-workload is the ragged survey batch: 10000 objects, N_t uniform in
-[50, 500] with a seasonal cadence, N_f = 100000 on [0.24, 12) c/d, FP32 sums
-with FP64/fixed-point phases, argmax only.
+trig-sum kernel with its fused power/argmax/top-3 epilogue and the finalize
+kernel, replayed as one CUDA graph (``lsp_plan_execute``) with the autotuned
+configuration.  The default workload is the largest batch: 100000 objects,
+N_t log-uniform in [10, 2000] with a seasonal cadence, N_f = 50000 on
+[0.24, 12) c/d, FP32 sums with FP64/fixed-point phases, argmax and top-3.
 
-One JSON line is printed by rank 0.  ``value`` is objects/s over all ranks
-(weak scaling: every rank runs its own batch of the same shape); ``e2e`` is
-the same metric through the host-buffer entry point with the copies inside
-the timed region; ``roofline`` relates the main kernel's measured pair rate
-to the FP32-pipe bound; ``cpu_baseline`` times the FP64 CPU oracle on a
-bounded sample of the same workload on this host's cores.
+One JSON line is printed by rank 0.  ``value`` is objects/s over all ranks;
+``e2e`` is the same metric through the host-buffer entry point with the
+copies inside the timed region; ``roofline`` relates the main kernel's
+measured pair rate to the FP32-pipe bound; ``cpu_baseline`` times the FP64
+CPU oracle on a bounded sample of the same workload on this host's cores;
+``learned`` (default workload, one GPU) times the learned proposal path
+(``lsp_propose_refine``, one call) against the plain full grid on 100000
+survey-shaped objects with N_f = 1e5, with its recovery of the full grid's
+periods.  Under torchrun the batch is sharded over the ranks by N_t
+(``shard.shard_ranges``; strong scaling) and the peaks are gathered on rank 0
+(``shard.gather_peaks``); ``--replicas`` gives every rank its own batch
+instead (weak scaling).
 
 ``--impl reference`` times the oracle alone (the CPU reference arm).
 """
@@ -60,6 +66,11 @@ WORKLOADS = {
 def dist_env():
     return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
             int(os.environ.get("LOCAL_RANK", 0)))
+
+
+DEFAULT_WORKLOAD = "ragged_lognormal"
+CHECKPOINT = os.path.join(ROOT, "paper_2105_04006_gb300", "weights", "proposer_survey.npz")
+LEARNED_N_OBJ = 100_000      # inference set of the learned path (survey-shaped, N_f = 1e5)
 
 
 def make_workload(name, rank, n_obj=None):
@@ -548,6 +559,91 @@ def run_ablations(args, lsp, torch, plan, b, t, y, off, name, rank):
     return 0
 
 
+def learned_leg(args, dev, gpu_index, log=None):
+    """The learned proposal path against the plain full grid on the same
+    100000 survey-shaped objects (N_t 50..500, N_f = 1e5 on [0.24, 12) c/d):
+    device time per step (CUDA events, L2 flushed), recovery of the full
+    grid's period (first maximum within one bin) and the cost breakdown."""
+    import torch
+    import paper_2105_04006_gb300 as lsp
+    from paper_2105_04006_gb300 import learned as L
+
+    ckpt = args.checkpoint or CHECKPOINT
+    if os.path.exists(ckpt):
+        prop, meta = L.Proposer.load_npz(ckpt, dev)
+        trained_on = f"{os.path.relpath(ckpt, ROOT)}: {meta.get('trained_on', 'committed network')}"
+    else:  # no committed network: train one on a bounded set in this run
+        n_train = args.n_train_inrun
+        per, sets = 25_000, []
+        for part in range((n_train + per - 1) // per):
+            sets.append(L.labelled_set(min(per, n_train - part * per), dev, "learned_train", part))
+        prop = L.Proposer(sets[0]["grid"].n_f, dev, seed=1)
+        L.train(prop, sets, epochs=10, batch_size=1024, lr=2e-3)
+        del sets
+        trained_on = f"{n_train} learned_train curves labelled by lsp_batch, trained in this run (10 epochs)"
+    b = synth.learned_set(LEARNED_N_OBJ, "learned_infer", 1000)
+    g = lsp.Grid(b.grid.f_min, b.grid.f_max, b.grid.n_f)
+    t = torch.tensor(b.t, dtype=torch.float64, device=dev)
+    y = torch.tensor(b.y.astype(np.float32), device=dev)
+    off = torch.tensor(b.offsets, dtype=torch.int64, device=dev)
+    plan = lsp.Plan(b.n_obj, b.t.size, g)
+    if not args.no_tune:  # the plain full grid at its fastest configuration
+        plan.autotune(t, y, off, cache_path=os.path.join(ROOT, "paper_2105_04006_gb300", "_build",
+                                                         "tune_cache.jsonl"))
+    peaks_plain = plan.peaks_buffer(dev)
+    path = L.LearnedPath(prop)
+    out = {}
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def timed(fn):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        ms = []
+        for i in range(args.steps):
+            flush.fill_(i & 0xFF)
+            a, c = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            fn()
+            c.record()
+            c.synchronize()
+            ms.append(a.elapsed_time(c))
+        return statistics.mean(ms)
+
+    def learned():
+        out["peaks"], out["info"] = path(t, y, off, g)
+
+    clk = ClockSampler(gpu_index)
+    clk.start()
+    clk.mark(0)
+    ms_plain = timed(lambda: plan.execute(t, y, off, peaks=peaks_plain))
+    ms_learned = timed(learned)
+    clk.mark(1)
+    clocks = clk.stop()
+    full = lsp.peaks_to_numpy(peaks_plain)
+    got = lsp.peaks_to_numpy(out["peaks"])
+    info = out["info"].cpu().numpy()
+    rounds = info & 255
+    fb = (info & L.REFINE_FALLBACK) != 0
+    ok = np.abs(got["idx"] - full["idx"]) <= 1
+    pairs = float(np.sum(b.n_t * (rounds * L.WINDOW + fb * g.n_f)))
+    cfg_plain = plan.config
+    plan.close()
+    return {"workload": "learned_infer", "shape": f"{b.n_obj} objects, N_t~U{{50..500}}, seasonal cadence, "
+                                                  "N_f=1e5 on [0.24,12) c/d, windows of 2048 bins, "
+                                                  f"top-{prop.k_windows} proposals, full-grid fallback below "
+                                                  f"P_n {prop.fallback_power}",
+            "value": b.n_obj / (ms_learned / 1e3), "unit": "objects/s", "ms_per_step": ms_learned,
+            "plain": {"value": b.n_obj / (ms_plain / 1e3), "ms_per_step": ms_plain, "kernel_config": cfg_plain},
+            "speedup_vs_plain": ms_plain / ms_learned,
+            "recovery": float(ok.mean()), "recovered_of": int(ok.size),
+            "fallback_fraction": float(fb.mean()), "mean_windows": float(rounds.mean()),
+            "pair_fraction": pairs / float(b.pairs), "stop_power": prop.stop_power,
+            "trained_on": trained_on, "entry_point": "lsp_propose_refine (one call per step)",
+            "steps": args.steps, "warmup": args.warmup, "l2": "flushed between steps (256 MiB write)",
+            "clocks": clocks}
+
+
 def run_gpu(args, w, name):
     import torch
     import paper_2105_04006_gb300 as lsp
@@ -560,7 +656,17 @@ def run_gpu(args, w, name):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
 
-    b = make_workload(name, rank, args.n_obj)
+    sharded = world > 1 and not args.replicas
+    if sharded:
+        # one batch, cut into N_t-balanced contiguous object ranges: rank r runs
+        # its own slice (no exchange on the data path)
+        from paper_2105_04006_gb300 import shard
+        full = make_workload(name, 0, args.n_obj)
+        ranges = shard.shard_ranges(full.offsets, world)
+        o0, o1 = ranges[rank]
+        b = full.subset(np.arange(o0, o1))
+    else:
+        b = make_workload(name, rank, args.n_obj)
     g = lsp.Grid(b.grid.f_min, b.grid.f_max, b.grid.n_f)
     fp64 = args.precision == "fp64"
     ydt = np.float64 if fp64 else np.float32
@@ -612,8 +718,14 @@ def run_gpu(args, w, name):
     if dist is not None:
         dist.all_reduce(total_s, op=dist.ReduceOp.MAX)
     total_s = float(total_s.item())
-    value = world * b.n_obj * args.steps / total_s
+    n_units = torch.tensor([b.n_obj], dtype=torch.float64, device=dev)  # objects this rank processed per step
+    if dist is not None:
+        dist.all_reduce(n_units)
+    value = float(n_units.item()) * args.steps / total_s
     pairs = b.pairs
+    gathered = None
+    if sharded:  # the only exchange: every rank's peak records to rank 0
+        gathered = shard.gather_peaks(lsp.peaks_to_numpy(peaks), ranges, rank, per_object=w["top_k"])
 
     # end to end through the host-buffer entry point (pinned host memory)
     th = torch.from_numpy(b.t).pin_memory()
@@ -642,7 +754,7 @@ def run_gpu(args, w, name):
     e2e_s = torch.tensor([sum(e2e_ms) / 1e3], dtype=torch.float64, device=dev)
     if dist is not None:
         dist.all_reduce(e2e_s, op=dist.ReduceOp.MAX)
-    e2e_value = world * b.n_obj * args.steps / float(e2e_s.item())
+    e2e_value = float(n_units.item()) * args.steps / float(e2e_s.item())
     ysz = 8 if fp64 else 4
     h2d = th.numel() * 8 + yh.numel() * ysz + (oh.numel() * 8 if oh is not None else 0)
     d2h = pk_host.nbytes + (ph.numel() * ysz if ph is not None else 0)
@@ -666,19 +778,25 @@ def run_gpu(args, w, name):
 
     line = None
     if rank == 0:
-        cpu = None if args.no_cpu else cpu_baseline(b, w["cpu_sample"], w["top_k"])
+        bb = full if sharded else b  # rank 0 checks the whole job's results
+        cpu = None if args.no_cpu else cpu_baseline(bb, w["cpu_sample"], w["top_k"])
         parity = None
         if cpu is not None:  # this run's own results against the oracle on the same sample
-            pk_np = lsp.peaks_to_numpy(peaks)
-            pw_np = power.cpu().numpy() if power is not None else None
+            pk_np = gathered if sharded else lsp.peaks_to_numpy(peaks)
+            pw_np = power.cpu().numpy() if (power is not None and not sharded) else None
             parity = parity_vs_oracle(getattr(cpu_baseline, "ref", None), pk_np, w["top_k"], pw_np, args.precision)
+        learned = None
+        if args.learned and world == 1 and not fp64:
+            learned = learned_leg(args, dev, gpu_index)
         line = {
             "impl": "gb300", "metric": METRIC, "value": value, "unit": "objects/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": statistics.mean(step_ms),
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64" if fp64 else "f32",
-            "data": "synthetic",
-            "config": {"workload": name, "shape": w["desc"], "n_obj": b.n_obj, "total_nt": int(b.t.size),
-                       "n_f": g.n_f,
+            "higher_is_better": True, "scaling": "strong" if sharded else "weak", "vs_baseline": None,
+            "dtype": "f64" if fp64 else "f32", "data": "synthetic",
+            "config": {"workload": name, "shape": w["desc"], "n_obj": int(n_units.item()),
+                       "total_nt": int(bb.t.size), "n_f": g.n_f,
+                       "parallelism": (f"objects sharded over {world} ranks by N_t" if sharded else
+                                       f"{world} independent replicas" if world > 1 else "1 GPU"),
                        "precision": "fp64" if fp64 else "fp32 sums, fp64/fixed-point phase",
                        "l2": "flushed between steps (256 MiB write)", "kernel_config": plan.config},
             "pairs_per_s": world * pairs * args.steps / total_s,
@@ -689,6 +807,9 @@ def run_gpu(args, w, name):
                          "measured_fma_rates_per_s": rates,
                          "frac_of_measured_pipe_ceiling": achieved / ceiling,
                          "kernel_ops_per_pair": KERNEL_OPS_PER_PAIR,
+                         "frac_note": (f"frac counts {OPS_PER_PAIR} FP32 operations per pair (the rotation "
+                                       f"recurrence's algorithmic work); the kernel issues {KERNEL_OPS_PER_PAIR}, "
+                                       "so its FP32 pipe is busy frac x 6/8 (pipe_busy_with_kernel_ops)"),
                          "pipe_busy_with_kernel_ops": (achieved * KERNEL_OPS_PER_PAIR / OPS_PER_PAIR / peak)
                          if (peak and not fp64) else achieved * KERNEL_OPS_PER_PAIR / OPS_PER_PAIR / ceiling,
                          "source_hash": src},
@@ -699,6 +820,7 @@ def run_gpu(args, w, name):
                     "ms_min": min(e2e_ms), "ms_max": max(e2e_ms), "clocks": clocks_e2e},
             "gpu_launches": plan.kernel_count * args.steps,
             "clocks": clocks,
+            "learned": learned,
         }
     plan.close()
     if dist is not None:
@@ -711,77 +833,39 @@ def run_gpu(args, w, name):
 
 # ------------------------------------------------------------ learned vs plain
 def run_learned(args):
-    """Learned proposal + refine against the plain full grid on the same batch."""
+    """Train the proposal network (unless the checkpoint exists), write it, and
+    time the learned path against the plain full grid (the learned leg)."""
     import torch
-    import paper_2105_04006_gb300 as lsp
     from paper_2105_04006_gb300 import learned as L
 
     rank, world, local = dist_env()
+    if world > 1:
+        raise SystemExit("--workload learned runs on one GPU")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    prop = None
-    if args.checkpoint and os.path.exists(args.checkpoint):
-        prop, _ = L.Proposer.load(args.checkpoint, dev)
-        trained_on = f"checkpoint {os.path.basename(args.checkpoint)}"
-    else:
+    ckpt = args.checkpoint or CHECKPOINT
+    train_s = None
+    if not os.path.exists(ckpt):
+        t0 = time.perf_counter()
         per, sets = 25_000, []
         for part in range((args.n_train + per - 1) // per):
             sets.append(L.labelled_set(min(per, args.n_train - part * per), dev, "learned_train", part))
         prop = L.Proposer(sets[0]["grid"].n_f, dev, seed=1)
-        L.train(prop, sets, epochs=10, batch_size=1024, lr=2e-3)
+        hist = L.train(prop, sets, epochs=10, batch_size=1024, lr=2e-3)
         del sets
-        trained_on = f"{args.n_train} learned_train curves labelled by lsp_batch, 10 epochs"
-        if args.checkpoint:
-            prop.save(args.checkpoint)
-    n_obj = args.n_obj or 100_000
-    test = L.labelled_set(n_obj, dev, "learned_infer", 1000 + rank)
-    b, g = test["batch"], test["grid"]
-    plan = lsp.Plan(b.n_obj, b.t.size, g)
-    if not args.no_tune:  # the plain full grid at its fastest configuration
-        plan.autotune(test["t"], test["y"], test["off"],
-                      cache_path=os.path.join(ROOT, "paper_2105_04006_gb300", "_build", "tune_cache.jsonl"))
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
-
-    def timed(fn):
-        for _ in range(args.warmup):
-            fn()
-        torch.cuda.synchronize()
-        ms = []
-        for i in range(args.steps):
-            flush.fill_(i & 0xFF)
-            a, c = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record()
-            fn()
-            c.record()
-            c.synchronize()
-            ms.append(a.elapsed_time(c))
-        return statistics.mean(ms)
-
-    clk = ClockSampler(os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[0])
-    clk.start()
-    clk.mark(0)
-    ms_plain = timed(lambda: plan.execute(test["t"], test["y"], test["off"]))
-    ms_learned = timed(lambda: L.propose_and_refine(prop, test["t"], test["y"], test["off"], g))
-    clk.mark(1)
-    clocks = clk.stop()
-    ev = L.evaluate(prop, test)
-    line = {
-        "impl": "gb300", "metric": METRIC, "value": b.n_obj / (ms_learned / 1e3), "unit": "objects/s",
-        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_learned,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": "learned", "shape": f"{b.n_obj} objects, N_t~U{{50..500}}, N_f=1e5, "
-                                                   "8 windows of 2048, fallback < 0.3",
-                   "trained_on": trained_on, "stop_power": prop.stop_power,
-                   "l2": "flushed between steps (256 MiB write)"},
-        "plain": {"value": b.n_obj / (ms_plain / 1e3), "ms_per_step": ms_plain, "kernel_config": plan.config},
-        "speedup_vs_plain": ms_plain / ms_learned,
-        "recovery": ev["recovery"], "fallback_fraction": ev["fallback"],
-        "mean_windows": ev["mean_windows"], "pair_fraction": ev["pair_fraction"],
-        "clocks": clocks,
-    }
-    plan.close()
-    if rank == 0:
-        print(json.dumps(line), flush=True)
+        train_s = time.perf_counter() - t0
+        os.makedirs(os.path.dirname(os.path.abspath(ckpt)), exist_ok=True)
+        prop.save_npz(ckpt, trained_on=(f"{args.n_train} learned_train curves (seeds disjoint from the inference "
+                                        "set) labelled by lsp_batch, 10 epochs of AdamW, batch 1024, "
+                                        f"lr 2e-3 cosine; final loss {hist[-1]:.4f}"))
+    gpu_index = os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[0]
+    leg = learned_leg(args, dev, gpu_index)
+    line = {"impl": "gb300", "metric": METRIC, "value": leg["value"], "unit": "objects/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": leg["ms_per_step"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic", "config": {"workload": "learned", "shape": leg["shape"]},
+            "training_s": train_s, "checkpoint": os.path.relpath(ckpt, ROOT), "learned": leg}
+    print(json.dumps(line), flush=True)
     return 0
 
 
@@ -791,9 +875,17 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["learned"], default="ragged_survey")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["learned"], default=DEFAULT_WORKLOAD)
     ap.add_argument("--n-train", type=int, default=1_000_000, help="learned workload: training curves")
-    ap.add_argument("--checkpoint", default=None, help="learned workload: proposer checkpoint to load/save")
+    ap.add_argument("--checkpoint", default=None,
+                    help="proposer network (.npz) to load (learned leg, learned workload) or to write (learned "
+                         "workload, when it does not exist); default: the committed network")
+    ap.add_argument("--no-learned", dest="learned", action="store_false",
+                    help="skip the learned-vs-plain leg of the default run")
+    ap.add_argument("--n-train-inrun", type=int, default=200_000,
+                    help="learned leg without a committed network: training curves generated in the run")
+    ap.add_argument("--replicas", action="store_true",
+                    help="under torchrun: every rank runs its own batch (weak scaling) instead of a shard of one")
     ap.add_argument("--no-tune", action="store_true", help="use the default kernel configuration")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
     ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")

@@ -52,7 +52,7 @@ def test_reference_arm_prints_the_contract_line():
         assert key in line, key
     assert line["impl"] == "reference" and line["value"] > 0 and line["steps"] == 1
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["cpu_baseline"]["kind"] == "oracle"
-    assert line["config"]["workload"] == "ragged_survey"
+    assert line["config"]["workload"] == "ragged_lognormal"  # the largest batch is the default
 
 
 def test_warmup_below_three_is_refused():
