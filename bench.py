@@ -644,6 +644,103 @@ def learned_leg(args, dev, gpu_index, log=None):
             "clocks": clocks}
 
 
+OTHER_LEGS = (("ragged_survey", "fp32"), ("single_small", "fp32"), ("single_small", "fp64"),
+              ("single_large", "fp32"), ("single_large", "fp64"))
+
+
+def other_leg(args, dev, name, precision, steps):
+    """One more workload of the same metric, measured like the main line but
+    compactly: autotuned plan, device time per step (L2 flushed), the main
+    kernel's time and fraction of its bound, and the run's error against the
+    oracle on a small sample (16 objects, or 200 frequencies of one object)."""
+    import torch
+    import paper_2105_04006_gb300 as lsp
+    import oracle
+
+    w = WORKLOADS[name]
+    b = make_workload(name, 0)
+    g = lsp.Grid(b.grid.f_min, b.grid.f_max, b.grid.n_f)
+    fp64 = precision == "fp64"
+    ydt = np.float64 if fp64 else np.float32
+    t = torch.tensor(b.t, dtype=torch.float64, device=dev)
+    y = torch.tensor(b.y.astype(ydt), device=dev)
+    off = torch.tensor(b.offsets, dtype=torch.int64, device=dev) if b.n_obj > 1 else None
+    power = (torch.empty((b.n_obj, g.n_f), dtype=torch.float64 if fp64 else torch.float32, device=dev)
+             if w["power"] else None)
+    plan = lsp.Plan(b.n_obj, b.t.size, g, top_k=w["top_k"], precision=precision)
+    # the FP64 path on the 1e11-pair object takes 1.3 s a step: its default
+    # configuration, no tuning
+    tuned = not args.no_tune and not (fp64 and b.pairs > 1e10)
+    if tuned:
+        plan.autotune(t, y, off, cache_path=os.path.join(ROOT, "paper_2105_04006_gb300", "_build", "tune_cache.jsonl"))
+    if fp64 and b.pairs > 1e10:
+        steps = min(steps, 5)
+    peaks = plan.peaks_buffer(dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def timed(probe):
+        # the step without the probe; the main kernel's time in a second pass
+        # with it (its event nodes add to a short step and keep the kernels
+        # from overlapping their launches)
+        plan.enable_timing(probe)
+        for _ in range(args.warmup):
+            plan.execute(t, y, off, power=power, peaks=peaks)
+        torch.cuda.synchronize()
+        step_ms, main_ms = [], []
+        for i in range(steps):
+            flush.fill_(i & 0xFF)
+            a, c = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            plan.execute(t, y, off, power=power, peaks=peaks)
+            c.record()
+            c.synchronize()
+            step_ms.append(a.elapsed_time(c))
+            if probe:
+                main_ms.append(plan.main_kernel_ms())
+        return statistics.mean(step_ms), (statistics.mean(main_ms) if main_ms else None)
+
+    st, _ = timed(False)
+    _, mk = timed(True)
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    achieved = b.pairs / (mk / 1e3) / 1e9
+    if fp64:
+        peak = lsp.probe_fma_rates(dev)["f64"] / OPS_PER_PAIR / 1e9
+        basis = f"measured DFMA rate / {OPS_PER_PAIR} ops per pair"
+    else:
+        peak = n_sm * FP32_LANES_PER_SM * 2070e6 / OPS_PER_PAIR / 1e9
+        basis = f"{n_sm} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2070 MHz / {OPS_PER_PAIR} ops per pair"
+    # the run's own error against the oracle on a small sample
+    oracle.build()
+    tol = 1e-10 if fp64 else 1e-4
+    yv = b.y.astype(ydt).astype(np.float64)
+    if b.n_obj == 1:
+        pw = power.reshape(-1).double().cpu().numpy()
+        ks = np.unique(np.concatenate([np.linspace(0, g.n_f - 1, 200).astype(np.int64),
+                                       [int(np.argmax(pw))]]))
+        ref, _ = oracle.lsp_single(b.t, yv, g.f_min, g.f_max, g.n_f, k_sel=ks)
+        par = {"compared": f"P_n at {ks.size} frequencies incl. the maximum", "max_abs_err": float(np.max(np.abs(
+            pw[ks] - ref))), "tolerance": tol}
+    else:
+        idx = np.linspace(0, b.n_obj - 1, 16).astype(np.int64)
+        sub = b.subset(idx)
+        res = oracle.lsp_batch(sub.t, sub.y.astype(ydt).astype(np.float64), sub.offsets, g.f_min, g.f_max, g.n_f,
+                               top_k=1)
+        first = lsp.peaks_to_numpy(peaks).reshape(-1, w["top_k"])[idx, 0]
+        dk = np.abs(first["idx"].astype(np.int64) - res["arg_idx"])
+        par = {"compared": f"first maximum of {idx.size} objects", "argmax_within_1_bin": float(np.mean(dk <= 1)),
+               "max_abs_err_peak_power": float(np.max(np.abs(first["power"] - res["arg_pow"]))), "tolerance": tol}
+    out = {"workload": name, "precision": precision, "shape": w["desc"], "value": b.n_obj / (st / 1e3),
+           "unit": "objects/s", "ms_per_step": st, "main_kernel_ms": mk, "pairs_per_s": b.pairs / (st / 1e3),
+           "timing": "step without the timing probe; main kernel from a second pass with it",
+           "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gpair/s",
+                        "frac": achieved / peak, "peak_basis": basis},
+           "kernel_config": plan.config, "autotuned": tuned, "gpu_launches_per_step": plan.kernel_count,
+           "steps": steps,
+           "parity_vs_oracle": par}
+    plan.close()
+    return out
+
+
 def run_gpu(args, w, name):
     import torch
     import paper_2105_04006_gb300 as lsp
@@ -788,6 +885,15 @@ def run_gpu(args, w, name):
         learned = None
         if args.learned and world == 1 and not fp64:
             learned = learned_leg(args, dev, gpu_index)
+        others = None
+        if args.others and world == 1 and name == DEFAULT_WORKLOAD and not fp64:
+            clk_o = ClockSampler(gpu_index)
+            clk_o.start()
+            clk_o.mark(0)
+            others = [other_leg(args, dev, n, pr, min(args.steps, 10)) for n, pr in OTHER_LEGS]
+            clk_o.mark(1)
+            others = {"legs": others, "clocks": clk_o.stop(),
+                      "note": "the other workloads of the same metric, each autotuned and timed on its own"}
         line = {
             "impl": "gb300", "metric": METRIC, "value": value, "unit": "objects/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": statistics.mean(step_ms),
@@ -821,6 +927,7 @@ def run_gpu(args, w, name):
             "gpu_launches": plan.kernel_count * args.steps,
             "clocks": clocks,
             "learned": learned,
+            "other_workloads": others,
         }
     plan.close()
     if dist is not None:
@@ -884,6 +991,8 @@ def main():
                     help="skip the learned-vs-plain leg of the default run")
     ap.add_argument("--n-train-inrun", type=int, default=200_000,
                     help="learned leg without a committed network: training curves generated in the run")
+    ap.add_argument("--no-others", dest="others", action="store_false",
+                    help="skip the compact legs of the other workloads in the default run")
     ap.add_argument("--replicas", action="store_true",
                     help="under torchrun: every rank runs its own batch (weak scaling) instead of a shard of one")
     ap.add_argument("--no-tune", action="store_true", help="use the default kernel configuration")

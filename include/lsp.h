@@ -317,12 +317,20 @@ lsp_status lsp_plan_get_host_parts(const lsp_plan* plan, int64_t power_bytes, in
 
 /*
  * Measure the candidate launch configurations on these inputs, keep the
- * fastest one whose powers stay within the FP32 error gate (1e-4 absolute
- * in P_n: the first object's periodogram against the FP64 path; skipped
- * when that object has fewer than two observations or offsets outside the
- * inputs), and use it from now on.  Synchronises `stream`.  When cache_path is not NULL the
- * choice is read from / appended to that JSON-lines file, keyed by device,
- * shape class and options.
+ * fastest one whose powers stay within the FP32 error gate, and use it from
+ * now on.  The gate compares each candidate's P_n with the FP64 path's,
+ * 1e-4 absolute at every grid frequency, on up to eight objects of the
+ * inputs: the first, the one with the most observations, the worst-
+ * conditioned of a pool (the largest R/N over the grid, R = |sum_j
+ * exp(4 pi i f t_j)|: where R approaches N, Eq. 2's smaller denominator
+ * (N - R)/2 is small and FP32 sums lose relative accuracy; the pool is the
+ * 32 shortest objects with three or more observations and 32 spread over
+ * the batch) and five spread over the batch.  Objects with fewer than two
+ * observations or offsets outside the inputs are left out; without any, the
+ * gate is skipped.  A single-object plan is gated on its object with each
+ * candidate's own split.  Synchronises `stream`.  When cache_path is not
+ * NULL the choice is read from / appended to that JSON-lines file, keyed by
+ * device, shape class and options.
  */
 lsp_status lsp_plan_autotune(lsp_plan* plan, const double* t, const void* y, const int64_t* offsets,
                              const char* cache_path, lsp_stream_t stream);
@@ -331,9 +339,9 @@ lsp_status lsp_plan_autotune(lsp_plan* plan, const double* t, const void* y, con
 typedef struct lsp_trial {
   lsp_config config;
   float ms;          /* time of one execution (mean of 3 graph replays), ms; -1 if not timed */
-  float max_err;     /* max |P_n - P_n(FP64)| on the first object (0 for FP64 plans) */
+  float max_err;     /* max |P_n - P_n(FP64)| over the gate's objects (0 for FP64 plans) */
   int32_t passed;    /* 1: within the error gate, so eligible (failed candidates are not timed) */
-  int32_t reserved;
+  int32_t worst_object; /* the gate object (batch index) with that error; -1 without a gate */
 } lsp_trial;
 
 #define LSP_TUNE_ABLATIONS 1  /* also measure the trig/staging ablation kernels (lsp_config) */
@@ -351,6 +359,15 @@ typedef struct lsp_trial {
 lsp_status lsp_plan_autotune_ex(lsp_plan* plan, const double* t, const void* y, const int64_t* offsets,
                                 const char* cache_path, int32_t flags, lsp_trial* trials,
                                 int32_t max_trials, int32_t* n_trials, lsp_stream_t stream);
+
+/*
+ * The last lsp_plan_autotune(_ex) error gate: its objects (batch indices,
+ * into objects) and, for the configuration it chose, each object's
+ * max |P_n - P_n(FP64)| (into max_err), at most cap of each; *n = the number
+ * of gate objects (0 after a cache hit or for FP64 plans).  Host only.
+ */
+lsp_status lsp_plan_gate_report(const lsp_plan* plan, int64_t* objects, float* max_err, int32_t cap,
+                                int32_t* n);
 
 /*
  * Timing probe.  While enabled, each execution of the plan also records two

@@ -73,7 +73,7 @@ class Config(ctypes.Structure):
 
 class Trial(ctypes.Structure):
     _fields_ = [("config", Config), ("ms", ctypes.c_float), ("max_err", ctypes.c_float),
-                ("passed", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("passed", ctypes.c_int32), ("worst_object", ctypes.c_int32)]
 
 
 TUNE_ABLATIONS = 1
@@ -93,6 +93,7 @@ EXPORTS = [
     "lsp_refine_windows", "lsp_batch_gls", "lsp_periodogram_gls", "lsp_workspace_size_gls",
     "lsp_probe_fma_rates", "lsp_plan_autotune_ex", "lsp_plan_set_host_parts", "lsp_plan_get_host_parts",
     "lsp_propose_refine", "lsp_propose_refine_workspace_size", "lsp_window_labels", "lsp_noalloc_prepare",
+    "lsp_plan_gate_report",
 ]
 
 
@@ -165,6 +166,7 @@ def lib():
             L.lsp_propose_refine.argtypes = [PP, P, P, P, i64, i64, GP, P, P, P, P, sz, P]
             L.lsp_window_labels.argtypes = [P, i64, i64, i32, P, P]
             L.lsp_noalloc_prepare.argtypes = []
+            L.lsp_plan_gate_report.argtypes = [P, P, P, i32, ctypes.POINTER(i32)]
             L.lsp_plan_destroy.argtypes = [P]
             L.lsp_plan_destroy.restype = None
             for name in EXPORTS:
@@ -537,5 +539,14 @@ class Plan:
                                           TUNE_ABLATIONS if ablations else 0, buf, 64, ctypes.byref(n),
                                           _stream_handle(t.device)))
         trials = [dict(config=buf[i].config.as_dict(), ms=float(buf[i].ms), max_err=float(buf[i].max_err),
-                       passed=bool(buf[i].passed)) for i in range(min(n.value, 64))]
+                       passed=bool(buf[i].passed), worst_object=int(buf[i].worst_object))
+                  for i in range(min(n.value, 64))]
         return (self.config, trials) if return_trials else self.config
+
+    def gate_report(self):
+        """The last autotune's error gate: [(object index, max |P_n - P_n(FP64)|)] for the chosen configuration."""
+        objs = (ctypes.c_int64 * 8)()
+        errs = (ctypes.c_float * 8)()
+        n = ctypes.c_int32(0)
+        _check(lib().lsp_plan_gate_report(self._h, objs, errs, 8, ctypes.byref(n)))
+        return [(int(objs[i]), float(errs[i])) for i in range(min(n.value, 8))]

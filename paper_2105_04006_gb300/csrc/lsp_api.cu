@@ -3,6 +3,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <algorithm>
 #include <cstring>
 #include <fstream>
 #include <mutex>
@@ -78,6 +79,7 @@ constexpr int64_t kMaxNf = (int64_t)1 << 31;  // k0 + F must fit in 32 bits
 constexpr int kMinObsPerSplit = 32;
 constexpr int kMaxObsPerSplit = 8192;  // bounds each FP32 partial sum
 constexpr int kMaxSplit = 256;
+constexpr int kGateObjects = 8;  // objects the autotuner's error gate checks
 
 lsp_status check_grid(const lsp_grid* g) {
   if (!g) return fail(LSP_E_ARG, "grid is NULL");
@@ -206,6 +208,12 @@ lsp_status resolve(int64_t n_obj, int64_t total_nt, const lsp_grid* g, const lsp
   return LSP_OK;
 }
 
+// One object given without offsets and short enough for the fused prologue
+// (statistics and records in one launch).
+bool fused_prologue(const Layout& L, const int64_t* offsets) {
+  return L.n_obj == 1 && !offsets && L.total_nt <= kFusedMaxNt;
+}
+
 // The launch sequence of one periodogram call (stream-ordered, no syncs).
 lsp_status run(const Layout& L, const double* t, const void* y, const int64_t* offsets,
                void* power_out, lsp_peak* peaks, char* ws, cudaStream_t st,
@@ -224,12 +232,18 @@ lsp_status run(const Layout& L, const double* t, const void* y, const int64_t* o
 
   // queue[0]: the main kernel's work counter; queue[1], queue[2]: last-CTA
   // tickets of the one-object statistics and combine kernels
-  LSP_CUDA(cudaMemsetAsync(queue, 0, 16, st), "queue reset");
-  LSP_CUDA(launch_stats(t, y, y64, offsets, L.n_obj, L.total_nt, L.center, L.norm, obj, st, L.gls != 0,
-                        dy, L.n_obj == 1 ? ws + L.off_stats : nullptr, queue + 1),
-           "prologue (statistics)");
-  LSP_CUDA(launch_records(t, y, y64, obj, L.n_obj, L.total_nt, L.f_min, L.df, y64, rec, st, L.gls != 0, dy),
-           "prologue (records)");
+  if (fused_prologue(L, offsets)) {  // one launch, which also clears the queue words
+    LSP_CUDA(launch_single_prologue(t, y, y64, L.total_nt, L.center, L.norm, L.f_min, L.df, y64, obj, rec, queue,
+                                    st, L.gls != 0, dy),
+             "prologue");
+  } else {
+    LSP_CUDA(cudaMemsetAsync(queue, 0, 16, st), "queue reset");
+    LSP_CUDA(launch_stats(t, y, y64, offsets, L.n_obj, L.total_nt, L.center, L.norm, obj, st, L.gls != 0,
+                          dy, L.n_obj == 1 ? ws + L.off_stats : nullptr, queue + 1),
+             "prologue (statistics)");
+    LSP_CUDA(launch_records(t, y, y64, obj, L.n_obj, L.total_nt, L.f_min, L.df, y64, rec, st, L.gls != 0, dy),
+             "prologue (records)");
+  }
   if (order) LSP_CUDA(launch_lpt_order(obj, L.n_obj, hist, order, st), "work-queue order");
   MainLaunch ml;
   ml.prec = L.prec;
@@ -457,6 +471,9 @@ struct lsp_plan {
   cudaStream_t copy_stream = nullptr;
   std::vector<cudaEvent_t> part_ev;
   cudaEvent_t copy_done = nullptr;
+  // the last autotune's error gate: objects and the chosen configuration's errors
+  std::vector<int64_t> gate_obj;
+  std::vector<double> gate_err;
 };
 
 namespace {
@@ -738,11 +755,24 @@ lsp_status lsp_plan_main_kernel_ms(lsp_plan* p, float* ms) {
 lsp_status lsp_plan_kernel_count(const lsp_plan* p, int32_t* count) {
   if (!p || !count) return fail(LSP_E_ARG, "NULL argument");
   const Layout& L = p->L;
-  // statistics + records + main (+ 3 for the LPT order) (+ combine) (+ finalize,
-  // which a split single object with a first-maximum output folds into the
-  // combine); peaks requested
+  // statistics + records (one fused launch for a short single object) + main
+  // (+ 3 for the LPT order) (+ combine) (+ finalize, which a split single
+  // object with a first-maximum output folds into the combine); peaks
+  // requested; plans of one object run without offsets
   const bool fused = L.split > 1 && !L.top;
-  *count = 3 + (L.n_obj > 1 ? 3 : 0) + (L.split > 1 ? 1 : 0) + (fused ? 0 : 1);
+  const bool one_prologue = L.n_obj == 1 && L.total_nt <= kFusedMaxNt;
+  *count = (one_prologue ? 2 : 3) + (L.n_obj > 1 ? 3 : 0) + (L.split > 1 ? 1 : 0) + (fused ? 0 : 1);
+  return LSP_OK;
+}
+
+lsp_status lsp_plan_gate_report(const lsp_plan* p, int64_t* objects, float* max_err, int32_t cap,
+                                int32_t* n) {
+  if (!p || !n || cap < 0 || (cap > 0 && (!objects || !max_err))) return fail(LSP_E_ARG, "bad argument");
+  *n = (int32_t)p->gate_obj.size();
+  for (int32_t i = 0; i < cap && i < *n; ++i) {
+    objects[i] = p->gate_obj[(size_t)i];
+    max_err[i] = i < (int32_t)p->gate_err.size() ? (float)p->gate_err[(size_t)i] : -1.0f;
+  }
   return LSP_OK;
 }
 
@@ -913,6 +943,8 @@ lsp_status lsp_plan_autotune_ex(lsp_plan* p, const double* t, const void* y, con
   cudaStream_t s = (cudaStream_t)stream;
   const std::string key = tune_key(p);
   lsp_config cached;
+  p->gate_obj.clear();
+  p->gate_err.clear();
   if (cache_path && !ablations && cache_lookup(cache_path, key, &cached)) {
     if (!apply_config(p, &cached)) return LSP_OK;
     g_err.clear();  // stale entry: tune again
@@ -959,20 +991,106 @@ lsp_status lsp_plan_autotune_ex(lsp_plan* p, const double* t, const void* y, con
     }
   }
 
-  // Error gate (FP32): the first object's periodogram against the FP64 path.
-  int64_t g_lo = 0, g_n = p->total_nt;
-  if (p->n_obj > 1) {
-    int64_t h[2];
-    LSP_CUDA(cudaMemcpyAsync(h, offsets, sizeof h, cudaMemcpyDeviceToHost, s), "offsets probe");
+  // Error gate (FP32): each candidate's periodograms of a few objects against
+  // the FP64 path -- the first object, the one with the most observations
+  // (the longest FP32 sums), the worst-conditioned one of a pool (the largest
+  // R/N of the spectral window at twice the frequency, where Eq. 2's smaller
+  // denominator (N - R)/2 is smallest relative to N) and objects spread over
+  // the batch.  Objects with fewer than two observations or offsets outside
+  // the inputs are left out.
+  std::vector<int64_t> gobj, gbeg, gcnt;
+  auto gate_add = [&](int64_t o, int64_t b0, int64_t n0) {
+    for (int64_t x : gobj)
+      if (x == o) return;
+    if (gobj.size() < (size_t)kGateObjects) {
+      gobj.push_back(o);
+      gbeg.push_back(b0);
+      gcnt.push_back(n0);
+    }
+  };
+  const bool fp32 = p->opts.precision == LSP_FP32;
+  if (fp32 && p->n_obj == 1) {
+    if (p->total_nt >= 2) gate_add(0, 0, p->total_nt);
+  } else if (fp32) {
+    std::vector<int64_t> off((size_t)p->n_obj + 1);
+    LSP_CUDA(cudaMemcpyAsync(off.data(), offsets, off.size() * sizeof(int64_t), cudaMemcpyDeviceToHost, s),
+             "offsets probe");
     LSP_CUDA(cudaStreamSynchronize(s), "offsets probe");
-    g_lo = h[0];
-    g_n = h[1] - h[0];
+    auto count = [&](int64_t o) -> int64_t {
+      const int64_t b0 = off[(size_t)o], e0 = off[(size_t)o + 1];
+      return (b0 >= 0 && e0 >= b0 && e0 <= p->total_nt) ? e0 - b0 : -1;
+    };
+    const int64_t n = p->n_obj;
+    int64_t longest = -1;
+    for (int64_t o = 0; o < n; ++o)
+      if (count(o) >= 2 && (longest < 0 || count(o) > count(longest))) longest = o;
+    std::vector<int64_t> spread;
+    for (int i = 0; i < 5; ++i) spread.push_back(n > 1 ? (n - 1) * i / 4 : 0);
+    // conditioning pool: the shortest objects (three observations or more)
+    // and objects spread by index
+    std::vector<int64_t> pool;
+    {
+      std::vector<std::pair<int64_t, int64_t>> by_n;
+      for (int64_t o = 0; o < n; ++o)
+        if (count(o) >= 3) by_n.push_back({count(o), o});
+      const size_t k = by_n.size() < 32 ? by_n.size() : 32;
+      std::partial_sort(by_n.begin(), by_n.begin() + k, by_n.end());
+      for (size_t i = 0; i < k; ++i) pool.push_back(by_n[i].second);
+      for (int i = 0; i < 32 && n > 0; ++i) {
+        const int64_t o = (n - 1) * i / 31;
+        if (count(o) >= 3 && std::find(pool.begin(), pool.end(), o) == pool.end()) pool.push_back(o);
+      }
+    }
+    int64_t worst = -1;
+    if (!pool.empty()) {
+      std::vector<int64_t> pb(pool.size()), pc(pool.size());
+      for (size_t i = 0; i < pool.size(); ++i) {
+        pb[i] = off[(size_t)pool[i]];
+        pc[i] = count(pool[i]);
+      }
+      int64_t* d_pool = nullptr;
+      float* d_score = nullptr;
+      std::vector<float> score(pool.size());
+      cudaError_t e = cudaMalloc(&d_pool, 2 * pool.size() * sizeof(int64_t));
+      if (e == cudaSuccess) e = cudaMalloc(&d_score, pool.size() * sizeof(float));
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(d_pool, pb.data(), pb.size() * sizeof(int64_t), cudaMemcpyHostToDevice, s);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(d_pool + pool.size(), pc.data(), pc.size() * sizeof(int64_t), cudaMemcpyHostToDevice, s);
+      if (e == cudaSuccess)
+        e = launch_window_score(t, d_pool, d_pool + pool.size(), (int)pool.size(), p->grid.f_min, p->L.df,
+                                p->grid.n_f, d_score, s);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(score.data(), d_score, score.size() * sizeof(float), cudaMemcpyDeviceToHost, s);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+      cudaFree(d_pool);
+      cudaFree(d_score);
+      if (e != cudaSuccess) return cuda_fail(e, "autotune conditioning score");
+      for (size_t i = 0; i < pool.size(); ++i)
+        if (worst < 0 || score[i] > score[(size_t)worst]) worst = (int64_t)i;
+      worst = pool[(size_t)worst];
+    }
+    for (int64_t o : {(int64_t)0, longest, worst})
+      if (o >= 0 && count(o) >= 2) gate_add(o, off[(size_t)o], count(o));
+    for (int64_t o : spread)
+      if (count(o) >= 2) gate_add(o, off[(size_t)o], count(o));
   }
-  // (the probe object must lie inside the inputs: the kernels flag bad
-  // offsets, but the gate reads this object's magnitudes directly)
-  const bool gate = p->opts.precision == LSP_FP32 && g_n >= 2 && g_lo >= 0 && g_n <= p->total_nt - g_lo;
-  double* ref = nullptr;   // FP64 periodogram of the probe object
+  const bool gate = !gobj.empty();
+  // a batch plan is gated as a batch of two or more objects (one object
+  // alone would take the split single-object path)
+  int64_t g_rows = (int64_t)gobj.size();
+  if (gate && p->n_obj > 1 && g_rows == 1) {
+    gbeg.push_back(gbeg[0]);
+    gcnt.push_back(gcnt[0]);
+    g_rows = 2;
+  }
+  int64_t g_total = 0;
+  for (int64_t c : gcnt) g_total += c;
+  double* ref = nullptr;   // FP64 periodograms of the gate objects
   double* y64 = nullptr;
+  double* gt = nullptr;    // the gate objects' observations, back to back
+  float* gy = nullptr;
+  int64_t* goff = nullptr;
   float* pw = nullptr;
   double* d_err = nullptr;
   char* gws = nullptr;
@@ -982,46 +1100,63 @@ lsp_status lsp_plan_autotune_ex(lsp_plan* p, const double* t, const void* y, con
   o64.k_reseed = o64.freqs_per_thread = o64.block_threads = o64.obs_split = 0;
   o64.top_k = 1;
   o64.norm = LSP_NORM_STANDARD;  // the gate compares P_n (1e-4 absolute)
+  lsp_opts o1 = p->opts;
+  o1.top_k = 1;
+  o1.norm = LSP_NORM_STANDARD;
   auto cleanup = [&]() {
     cudaFree(ref);
     cudaFree(y64);
+    cudaFree(gt);
+    cudaFree(gy);
+    cudaFree(goff);
     cudaFree(pw);
     cudaFree(d_err);
     cudaFree(gws);
   };
+  const int64_t g_nobj = p->n_obj == 1 ? 1 : g_rows;
   if (gate) {
     Layout L64;
-    if ((st = resolve(1, g_n, &p->grid, &o64, nullptr, &L64))) return st;
+    if ((st = resolve(g_nobj, g_total, &p->grid, &o64, nullptr, &L64))) return st;
     gws_bytes = L64.total;
-    {  // room for every candidate's single-object layout too
-      for (const auto& c : cands) {
-        Layout Lc;
-        lsp_config c1 = c;
-        c1.obs_split = 1;
-        lsp_opts o1 = p->opts;
-        o1.top_k = 1;
-        o1.norm = LSP_NORM_STANDARD;
-        if (!resolve(1, g_n, &p->grid, &o1, &c1, &Lc) && Lc.total > gws_bytes) gws_bytes = Lc.total;
-      }
+    for (const auto& c : cands) {  // room for every candidate's layout too
+      Layout Lc;
+      if (!resolve(g_nobj, g_total, &p->grid, &o1, &c, &Lc) && Lc.total > gws_bytes) gws_bytes = Lc.total;
     }
-    if (cudaMalloc(&ref, p->grid.n_f * sizeof(double)) || cudaMalloc(&y64, g_n * sizeof(double)) ||
-        cudaMalloc(&pw, p->grid.n_f * sizeof(float)) || cudaMalloc(&d_err, sizeof(double)) ||
-        cudaMalloc(&gws, gws_bytes)) {
+    g_err.clear();
+    const size_t rows = (size_t)g_rows;
+    if (cudaMalloc(&ref, rows * p->grid.n_f * sizeof(double)) || cudaMalloc(&y64, g_total * sizeof(double)) ||
+        cudaMalloc(&gt, g_total * sizeof(double)) || cudaMalloc(&gy, g_total * sizeof(float)) ||
+        cudaMalloc(&goff, (rows + 1) * sizeof(int64_t)) || cudaMalloc(&pw, rows * p->grid.n_f * sizeof(float)) ||
+        cudaMalloc(&d_err, rows * sizeof(double)) || cudaMalloc(&gws, gws_bytes)) {
       cudaGetLastError();
       cleanup();
       return fail(LSP_E_NOMEM, "autotune scratch");
     }
-    cudaError_t e = launch_f32_to_f64((const float*)y + g_lo, y64, g_n, s);
-    if (e != cudaSuccess) { cleanup(); return cuda_fail(e, "autotune convert"); }
-    if ((st = run(L64, t + g_lo, y64, nullptr, ref, nullptr, gws, s))) { cleanup(); return st; }
+    std::vector<int64_t> hoff(rows + 1, 0);
+    cudaError_t e = cudaSuccess;
+    for (size_t i = 0; i < rows && e == cudaSuccess; ++i) {
+      hoff[i + 1] = hoff[i] + gcnt[i];
+      e = cudaMemcpyAsync(gt + hoff[i], t + gbeg[i], gcnt[i] * sizeof(double), cudaMemcpyDeviceToDevice, s);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(gy + hoff[i], (const float*)y + gbeg[i], gcnt[i] * sizeof(float),
+                            cudaMemcpyDeviceToDevice, s);
+    }
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(goff, hoff.data(), hoff.size() * sizeof(int64_t), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = launch_f32_to_f64(gy, y64, g_total, s);
+    // the host offsets must outlive the copy
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) { cleanup(); return cuda_fail(e, "autotune gate inputs"); }
+    if ((st = run(L64, gt, y64, g_nobj > 1 ? goff : nullptr, ref, nullptr, gws, s))) { cleanup(); return st; }
   }
+  std::vector<double> cur_err((size_t)g_rows), best_obj_err;
 
   float best_ms = 1e30f;
   double best_err = 0.0;
   lsp_config best = p->cfg;
   bool any = false;
   int32_t n_meas = 0;
-  auto record = [&](const lsp_config& c, float ms, double err, bool passed) {
+  auto record = [&](const lsp_config& c, float ms, double err, bool passed, int64_t worst_obj) {
     if (n_meas < max_trials) {
       lsp_trial& tr = trials[n_meas];
       memset(&tr, 0, sizeof tr);
@@ -1029,6 +1164,7 @@ lsp_status lsp_plan_autotune_ex(lsp_plan* p, const double* t, const void* y, con
       tr.ms = ms;
       tr.max_err = (float)err;
       tr.passed = passed ? 1 : 0;
+      tr.worst_object = (int32_t)worst_obj;
     }
     ++n_meas;
     if (n_trials) *n_trials = n_meas;
@@ -1037,21 +1173,24 @@ lsp_status lsp_plan_autotune_ex(lsp_plan* p, const double* t, const void* y, con
     Layout Lc;
     if (resolve(p->n_obj, p->total_nt, &p->grid, &p->opts, &c, &Lc)) { g_err.clear(); continue; }
     double err = 0.0;
+    int64_t worst_obj = -1;
     if (gate) {
+      // the candidate's own configuration (a single object keeps its split)
       Layout Lg;
-      lsp_config c1 = c;
-      c1.obs_split = 1;
-      lsp_opts o1 = p->opts;
-      o1.top_k = 1;
-      o1.norm = LSP_NORM_STANDARD;
-      if (resolve(1, g_n, &p->grid, &o1, &c1, &Lg)) { g_err.clear(); continue; }
-      if ((st = run(Lg, t + g_lo, (const float*)y + g_lo, nullptr, pw, nullptr, gws, s))) { cleanup(); return st; }
-      cudaError_t e = launch_max_abs_diff(pw, ref, p->grid.n_f, d_err, s);
-      if (e == cudaSuccess) e = cudaMemcpyAsync(&err, d_err, sizeof(double), cudaMemcpyDeviceToHost, s);
+      if (resolve(g_nobj, g_total, &p->grid, &o1, &c, &Lg)) { g_err.clear(); continue; }
+      if ((st = run(Lg, gt, gy, g_nobj > 1 ? goff : nullptr, pw, nullptr, gws, s))) { cleanup(); return st; }
+      cudaError_t e = launch_row_max_abs_diff(pw, ref, g_rows, p->grid.n_f, d_err, s);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(cur_err.data(), d_err, cur_err.size() * sizeof(double), cudaMemcpyDeviceToHost, s);
       if (e == cudaSuccess) e = cudaStreamSynchronize(s);
       if (e != cudaSuccess) { cleanup(); return cuda_fail(e, "autotune gate"); }
+      for (size_t i = 0; i < gobj.size(); ++i)
+        if (!(cur_err[i] <= err)) {  // NaN counts as the worst
+          err = std::isnan(cur_err[i]) ? INFINITY : cur_err[i];
+          worst_obj = gobj[i];
+        }
       if (!(err <= 1e-4)) {
-        record(c, -1.f, err, false);
+        record(c, -1.f, err, false, worst_obj);
         continue;
       }
     }
@@ -1062,17 +1201,20 @@ lsp_status lsp_plan_autotune_ex(lsp_plan* p, const double* t, const void* y, con
     st = time_runs(p, t, y, offsets, 3, s, &ms);
     p->L = saved;
     if (st) { cleanup(); return st; }
-    record(config_of(Lc), ms, err, true);
+    record(config_of(Lc), ms, err, true, worst_obj);
     if (ms < best_ms) {
       best_ms = ms;
       best = config_of(Lc);
       best_err = err;
+      best_obj_err.assign(cur_err.begin(), cur_err.begin() + (gate ? (ptrdiff_t)gobj.size() : 0));
       any = true;
     }
   }
   cleanup();
   if (!any) return fail(LSP_E_NUMERIC, "no candidate configuration passed the error gate");
   if ((st = apply_config(p, &best))) return st;
+  p->gate_obj = gobj;
+  p->gate_err.assign(best_obj_err.begin(), best_obj_err.end());
   if (cache_path) cache_store(cache_path, key, best, best_ms, best_err);
   return LSP_OK;
 }

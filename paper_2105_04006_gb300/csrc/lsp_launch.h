@@ -38,7 +38,16 @@ cudaError_t launch_records(const double* t, const void* y, bool y64, const ObjIn
                            int64_t n_obj, int64_t max_nt_single, double f_min, double df,
                            bool rec64, void* rec, cudaStream_t stream, bool gls = false,
                            const void* dy = nullptr);
-// Objects ordered by decreasing N_t (counting sort).
+// One object of at most kFusedMaxNt observations: statistics and records in
+// one launch, which also clears the four work-counter words at `queue` (no
+// memset, no ticket).  Every CTA redoes the object's FP64 statistics, about
+// 3.5 clocks per observation on one SM at GB300's FP64 rate, which caps it.
+constexpr int64_t kFusedMaxNt = 2048;
+cudaError_t launch_single_prologue(const double* t, const void* y, bool y64, int64_t n, int center, int norm,
+                                   double f_min, double df, bool rec64, ObjInfo* obj, void* rec, uint32_t* queue,
+                                   cudaStream_t stream, bool gls = false, const void* dy = nullptr);
+// The work-queue order: objects by N_t (counting sort), the longest and the
+// shortest alternating.
 cudaError_t launch_lpt_order(const ObjInfo* obj, int64_t n_obj, uint32_t* hist, int32_t* order,
                              cudaStream_t stream);
 
@@ -82,7 +91,10 @@ size_t main_dyn_smem(int prec, int fpt, int threads, int top);
 // peaks, no candidates and a zeroed ticket word it also writes the first
 // maximum (no finalize launch needed).
 constexpr int kCombineThreads = 256;
-constexpr int kCombinePerThread = 4;
+#ifndef LSP_COMBINE_PER_THREAD
+#define LSP_COMBINE_PER_THREAD 1
+#endif
+constexpr int kCombinePerThread = LSP_COMBINE_PER_THREAD;
 cudaError_t launch_combine(int prec, const void* part, int split, int64_t n_f, const ObjInfo* obj,
                            const void* rec, void* power_out, ChunkBest* best, ChunkCand* cand,
                            cudaStream_t stream, lsp_peak* peaks = nullptr, double f_min = 0.0,
@@ -102,5 +114,12 @@ cudaError_t launch_argmax_period(const void* power, bool p64, int64_t n_obj, int
 cudaError_t launch_f32_to_f64(const float* a, double* b, int64_t n, cudaStream_t stream);
 cudaError_t launch_max_abs_diff(const float* a, const double* b, int64_t n, double* out,
                                 cudaStream_t stream);
+// out[r] = max_i |a[r n + i] - b[r n + i]| for each of `rows` rows.
+cudaError_t launch_row_max_abs_diff(const float* a, const double* b, int64_t rows, int64_t n, double* out,
+                                    cudaStream_t stream);
+// score[i] = max over the grid of |sum_j exp(2 pi i 2 f_k t_j)| / N for the
+// observations t[begin[i] .. begin[i] + count[i]) (device arrays).
+cudaError_t launch_window_score(const double* t, const int64_t* begin, const int64_t* count, int n_list,
+                                double f_min, double df, int64_t n_f, float* score, cudaStream_t stream);
 
 }  // namespace lsp

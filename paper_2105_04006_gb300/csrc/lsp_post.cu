@@ -144,11 +144,13 @@ __global__ void __launch_bounds__(kCombineThreads) combine_kernel(
     s_last = atomicAdd(ticket, 1u) == gridDim.x - 1;
   }
   __syncthreads();
-  if (!s_last || threadIdx.x >= 32) return;
+  if (!s_last) return;
   __threadfence();
+  // the whole last CTA merges the chunk results (first maximum: the larger
+  // power, the lower bin on a tie, so the order of merging does not matter)
   double p = 0.0;
   int64_t k = -1;
-  for (unsigned c = threadIdx.x; c < gridDim.x; c += 32) {
+  for (unsigned c = threadIdx.x; c < gridDim.x; c += blockDim.x) {
     const double bp = __ldcg(&best[c].p);
     const int64_t bk = __ldcg(&best[c].k);
     if (better(bp, bk, p, k)) {
@@ -156,6 +158,16 @@ __global__ void __launch_bounds__(kCombineThreads) combine_kernel(
       k = bk;
     }
   }
+  warp_best(p, k);
+  const int w = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0) {
+    red_p[w] = p;
+    red_k[w] = k;
+  }
+  __syncthreads();
+  if (threadIdx.x >= 32) return;
+  p = threadIdx.x < (blockDim.x >> 5) ? red_p[threadIdx.x] : 0.0;
+  k = threadIdx.x < (blockDim.x >> 5) ? red_k[threadIdx.x] : -1;
   warp_best(p, k);
   if (threadIdx.x == 0) peaks[0] = make_peak(k, p, f_min, df, oi.flags);
 }
@@ -342,7 +354,81 @@ __global__ void max_abs_diff_kernel(const float* __restrict__ a, const double* _
   if (threadIdx.x == 0) atomicMax(out, m);
 }
 
+// Per row of n values: max_i |a_i - b_i| into out[row] (bits of a non-negative double).
+__global__ void row_max_abs_diff_kernel(const float* __restrict__ a, const double* __restrict__ b, int64_t n,
+                                        unsigned long long* out) {
+  __shared__ unsigned long long sh[32];
+  const int64_t row = blockIdx.y;
+  const float* ar = a + row * n;
+  const double* br = b + row * n;
+  unsigned long long m = 0ull;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    double d = fabs((double)ar[i] - br[i]);
+    if (isnan(d)) d = INFINITY;
+    const unsigned long long v = (unsigned long long)__double_as_longlong(d);
+    m = v > m ? v : m;
+  }
+  m = block_max_u64<double>(m, sh);
+  if (threadIdx.x == 0) atomicMax(out + row, m);
+}
+
+// Conditioning of Eq. 2's denominators for object i of a list: the largest
+// R / N over the grid, R = |sum_j exp(2 pi i (2 f_k) t_j)| (the spectral
+// window at twice the frequency).  Where R approaches N, one of the two
+// tau-shifted sums of squares, (N - R)/2, is small and FP32 sums lose
+// relative accuracy.  Phases are reduced in FP64 against the object's first
+// time (R does not depend on the origin); sin/cos and the sums are FP32.
+__global__ void window_score_kernel(const double* __restrict__ t, const int64_t* __restrict__ begin,
+                                    const int64_t* __restrict__ count, double f_min, double df, int64_t n_f,
+                                    unsigned int* __restrict__ score_bits) {
+  __shared__ unsigned long long sh[32];
+  const int i = blockIdx.y;
+  const int64_t b = begin[i], n = count[i];
+  const double t_ref = n > 0 ? t[b] : 0.0;
+  float best = 0.0f;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n_f; k += (int64_t)gridDim.x * blockDim.x) {
+    const double f2 = 2.0 * (f_min + (double)k * df);
+    float c = 0.0f, s = 0.0f;
+    for (int64_t j = 0; j < n; ++j) {
+      double ph = f2 * (t[b + j] - t_ref);
+      ph -= rint(ph);
+      float sj, cj;
+      sincospif((float)(2.0 * ph), &sj, &cj);
+      c += cj;
+      s += sj;
+    }
+    const float r = n > 0 ? sqrtf(c * c + s * s) / (float)n : 0.0f;
+    best = r > best ? r : best;
+  }
+  unsigned long long m = (unsigned long long)__float_as_uint(best);  // non-negative: bits order as values
+  m = block_max_u64<double>(m, sh);
+  if (threadIdx.x == 0) atomicMax(score_bits + i, (unsigned int)m);
+}
+
 }  // namespace
+
+cudaError_t launch_row_max_abs_diff(const float* a, const double* b, int64_t rows, int64_t n, double* out,
+                                    cudaStream_t stream) {
+  if (rows <= 0) return cudaSuccess;
+  cudaError_t e = cudaMemsetAsync(out, 0, (size_t)rows * sizeof(double), stream);
+  if (e != cudaSuccess || n <= 0) return e;
+  const int64_t per = (n + 255) / 256;
+  dim3 grid((unsigned)(per < 128 ? per : 128), (unsigned)rows);
+  row_max_abs_diff_kernel<<<grid, 256, 0, stream>>>(a, b, n, reinterpret_cast<unsigned long long*>(out));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_window_score(const double* t, const int64_t* begin, const int64_t* count, int n_list,
+                                double f_min, double df, int64_t n_f, float* score, cudaStream_t stream) {
+  if (n_list <= 0) return cudaSuccess;
+  cudaError_t e = cudaMemsetAsync(score, 0, (size_t)n_list * sizeof(float), stream);
+  if (e != cudaSuccess || n_f <= 0) return e;
+  const int64_t per = (n_f + 255) / 256;
+  dim3 grid((unsigned)(per < 64 ? per : 64), (unsigned)n_list);
+  window_score_kernel<<<grid, 256, 0, stream>>>(t, begin, count, f_min, df, n_f,
+                                                reinterpret_cast<unsigned int*>(score));
+  return cudaGetLastError();
+}
 
 cudaError_t launch_f32_to_f64(const float* a, double* b, int64_t n, cudaStream_t stream) {
   if (n <= 0) return cudaSuccess;

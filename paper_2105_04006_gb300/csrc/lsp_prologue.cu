@@ -76,46 +76,66 @@ __device__ double block_max(double v, double* sh) {
 // real arithmetic as s2 - 2 d sy + d^2 sw with d = mean - K; in FP64 the
 // shift keeps the cancellation to a few digits of the 16.  GLS: w = 1/dy^2
 // (dy NULL: unit weights) for the generalized periodogram.
+//
+// GB300 runs FP64 at 1/64 of the FP32 rate, so only the two (GLS: three)
+// sums use FP64 arithmetic: the time span is kept as order-preserving 64-bit
+// integer keys of the FP64 times (exact min/max on the integer pipe), and
+// without weights sw is the observation count, supplied at the end.
 struct StatAcc {
-  double sy, sw, s2, tmin, tmax, bad;
+  double sy, sw, s2;
+  unsigned long long tmin, tmax;  // time_key of the earliest / latest time
+  unsigned long long bad;         // non-zero: a NaN or Inf was seen
 };
 constexpr int kStatSlice = 256;  // observations (and threads) per CTA of the one-object pass
 
-__device__ __forceinline__ StatAcc stat_identity() { return StatAcc{0.0, 0.0, 0.0, INFINITY, -INFINITY, 0.0}; }
-
-__device__ __forceinline__ void stat_merge(StatAcc& a, const StatAcc& b) {
-  a.sy += b.sy;
-  a.sw += b.sw;
-  a.s2 += b.s2;
-  a.tmin = fmin(a.tmin, b.tmin);
-  a.tmax = fmax(a.tmax, b.tmax);
-  a.bad += b.bad;
+// An unsigned key that orders like the FP64 value (finite values and infinities).
+__device__ __forceinline__ unsigned long long time_key(double v) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+__device__ __forceinline__ double time_of_key(unsigned long long k) {
+  const unsigned long long b = (k >> 63) ? (k & 0x7fffffffffffffffull) : ~k;
+  return __longlong_as_double((long long)b);
 }
 
+__device__ __forceinline__ StatAcc stat_identity() { return StatAcc{0.0, 0.0, 0.0, ~0ull, 0ull, 0ull}; }
+
+template <bool GLS>
+__device__ __forceinline__ void stat_merge(StatAcc& a, const StatAcc& b) {
+  a.sy += b.sy;
+  if (GLS) a.sw += b.sw;
+  a.s2 += b.s2;
+  a.tmin = b.tmin < a.tmin ? b.tmin : a.tmin;
+  a.tmax = b.tmax > a.tmax ? b.tmax : a.tmax;
+  a.bad |= b.bad;
+}
+
+template <bool GLS>
 __device__ __forceinline__ void stat_warp_merge(StatAcc& a) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     StatAcc b;
     b.sy = __shfl_xor_sync(0xffffffffu, a.sy, o);
-    b.sw = __shfl_xor_sync(0xffffffffu, a.sw, o);
+    b.sw = GLS ? __shfl_xor_sync(0xffffffffu, a.sw, o) : 0.0;
     b.s2 = __shfl_xor_sync(0xffffffffu, a.s2, o);
     b.tmin = __shfl_xor_sync(0xffffffffu, a.tmin, o);
     b.tmax = __shfl_xor_sync(0xffffffffu, a.tmax, o);
     b.bad = __shfl_xor_sync(0xffffffffu, a.bad, o);
-    stat_merge(a, b);
+    stat_merge<GLS>(a, b);
   }
 }
 
 // Block reduction of StatAcc; the result is valid in thread 0.  sh holds one
 // StatAcc per warp.
+template <bool GLS>
 __device__ __forceinline__ StatAcc stat_block_merge(StatAcc a, StatAcc* sh) {
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
-  stat_warp_merge(a);
+  stat_warp_merge<GLS>(a);
   if (l == 0) sh[w] = a;
   __syncthreads();
   if (w == 0) {
     a = l < nw ? sh[l] : stat_identity();
-    stat_warp_merge(a);
+    stat_warp_merge<GLS>(a);
   }
   __syncthreads();
   return a;
@@ -130,30 +150,38 @@ __device__ __forceinline__ void stat_accumulate(const double* __restrict__ t, co
     double wj = 1.0;
     if (GLS && dy) {
       const double ej = (double)dy[j];
-      if (!isfinite(ej) || !(ej > 0.0)) a.bad = 1.0;
+      if (!isfinite(ej) || !(ej > 0.0)) a.bad = 1ull;
       wj = 1.0 / (ej * ej);
     }
-    if (!isfinite(tj) || !isfinite(yj)) a.bad = 1.0;
+    if (!isfinite(tj) || !isfinite(yj)) a.bad = 1ull;
     const double d = yj - K;
-    a.sy = fma(wj, d, a.sy);
-    a.sw += wj;
-    a.s2 = fma(wj * d, d, a.s2);
-    a.tmin = fmin(a.tmin, tj);
-    a.tmax = fmax(a.tmax, tj);
+    if (GLS) {
+      a.sy = fma(wj, d, a.sy);
+      a.sw += wj;
+      a.s2 = fma(wj * d, d, a.s2);
+    } else {
+      a.sy += d;
+      a.s2 = fma(d, d, a.s2);
+    }
+    const unsigned long long k = time_key(tj);
+    a.tmin = k < a.tmin ? k : a.tmin;
+    a.tmax = k > a.tmax ? k : a.tmax;
   }
 }
 
 template <bool GLS>
-__device__ __forceinline__ ObjInfo stat_finish(const StatAcc& a, double K, int64_t b, int64_t n, int flags,
+__device__ __forceinline__ ObjInfo stat_finish(const StatAcc& acc, double K, int64_t b, int64_t n, int flags,
                                                int center) {
+  StatAcc a = acc;
+  if (!GLS) a.sw = (double)n;  // unit weights: the sum of weights is the count
   const double mean = ((GLS || center) && n > 0 && a.sw > 0.0) ? K + a.sy / a.sw : 0.0;
   const double d = mean - K;
   const double s2 = n > 0 ? a.s2 - 2.0 * d * a.sy + d * d * a.sw : 0.0;
-  if (a.bad > 0.0) flags |= LSP_FLAG_NONFINITE;
+  if (a.bad) flags |= LSP_FLAG_NONFINITE;
   if (n < (GLS ? 3 : 2)) flags |= LSP_FLAG_FEW_OBS;
   if (!(flags & LSP_FLAG_NONFINITE) && n > 0 && !(s2 > 0.0)) flags |= LSP_FLAG_ZERO_VAR;
   ObjInfo oi;
-  oi.t0 = n > 0 ? 0.5 * (a.tmin + a.tmax) : 0.0;
+  oi.t0 = n > 0 ? 0.5 * (time_of_key(a.tmin) + time_of_key(a.tmax)) : 0.0;
   oi.ymean = mean;
   oi.sum_y2 = s2;
   oi.begin = b;
@@ -193,7 +221,7 @@ __global__ void stats_kernel(const double* __restrict__ t, const YT* __restrict_
   const double K = n > 0 ? (double)y[b] : 0.0;
   StatAcc a = stat_identity();
   stat_accumulate<YT, GLS>(t, y, dy, b, e, K, a);
-  a = stat_block_merge(a, sh);
+  a = stat_block_merge<GLS>(a, sh);
   if (threadIdx.x == 0) {
     ObjInfo oi = stat_finish<GLS>(a, K, b, n, flags, center);
     stat_norm(oi, norm, GLS);
@@ -216,7 +244,7 @@ __global__ void stats_slices_kernel(const double* __restrict__ t, const YT* __re
   const int64_t e = b + slice < n ? b + slice : n;
   StatAcc a = stat_identity();
   stat_accumulate<YT, GLS>(t, y, dy, b, e, K, a);
-  a = stat_block_merge(a, sh);
+  a = stat_block_merge<GLS>(a, sh);
   if (threadIdx.x == 0) {
     part[blockIdx.x] = a;
     __threadfence();
@@ -228,10 +256,11 @@ __global__ void stats_slices_kernel(const double* __restrict__ t, const YT* __re
   StatAcc r = stat_identity();
   for (unsigned s = threadIdx.x; s < gridDim.x; s += 32) {
     const double* q = reinterpret_cast<const double*>(part + s);
-    StatAcc v{__ldcg(q), __ldcg(q + 1), __ldcg(q + 2), __ldcg(q + 3), __ldcg(q + 4), __ldcg(q + 5)};
-    stat_merge(r, v);
+    const unsigned long long* u = reinterpret_cast<const unsigned long long*>(part + s);
+    StatAcc v{__ldcg(q), __ldcg(q + 1), __ldcg(q + 2), __ldcg(u + 3), __ldcg(u + 4), __ldcg(u + 5)};
+    stat_merge<GLS>(r, v);
   }
-  stat_warp_merge(r);
+  stat_warp_merge<GLS>(r);
   if (threadIdx.x == 0) {
     ObjInfo oi = stat_finish<GLS>(r, K, 0, n, n > (int64_t)INT32_MAX ? LSP_FLAG_BAD_OFFSETS : 0, center);
     stat_norm(oi, norm, GLS);
@@ -250,6 +279,58 @@ __device__ __forceinline__ uint64_t frac_fixed64(double f, double x) {
   return u + (uint64_t)corr;
 }
 
+// The record of observation j of an object (statistics oi).
+template <typename YT, typename Rec, bool GLS>
+__device__ __forceinline__ void make_record(const double* __restrict__ t, const YT* __restrict__ y,
+                                            const YT* __restrict__ dy, int64_t j, const ObjInfo& oi, double f_min,
+                                            double df, Rec* __restrict__ rec) {
+  const double tp = t[j] - oi.t0;
+  const uint64_t a = frac_fixed64(f_min, tp);
+  const uint64_t bb = frac_fixed64(df, tp);
+  const double xb = (double)(int64_t)bb * 5.421010862427522e-20;  // 2^-64: cycles in [-1/2, 1/2)
+  double s, c;
+  if constexpr (sizeof(Rec) == sizeof(RecF32)) {
+    // FP32 rotation: sincospi of the fraction's leading float, corrected to
+    // first order for the remainder (|lo| < 2^-25 cycle): accurate to about
+    // one FP32 ulp without an FP64 transcendental (GB300's FP64 pipe is
+    // 1/64 of its FP32 rate).
+    const float hi = (float)xb;
+    const float lo = (float)(xb - (double)hi);
+    float sh, ch;
+    sincospif(2.0f * hi, &sh, &ch);
+    const float d = 6.28318530717958647692f * lo;
+    c = (double)fmaf(-sh, d, ch);
+    s = (double)fmaf(ch, d, sh);
+  } else {
+    sincospi(2.0 * xb, &s, &c);
+  }
+  double w = 1.0;
+  if (GLS && dy) {
+    const double ej = (double)dy[j];
+    w = 1.0 / (ej * ej);
+  }
+  const double yc = (GLS ? w : 1.0) * ((double)y[j] - oi.ymean);
+  Rec r;
+  if constexpr (sizeof(Rec) == sizeof(RecF32)) {
+    r.y = (float)yc;
+    r.cr = (float)c;
+    r.sr = (float)s;
+    r.a_hi = (uint32_t)(a >> 32);
+    r.a_lo = (uint32_t)a;
+    r.b_hi = (uint32_t)(bb >> 32);
+    r.b_lo = (uint32_t)bb;
+    r.pad = GLS ? __float_as_uint((float)w) : 0u;
+  } else {
+    r.y = yc;
+    r.cr = c;
+    r.sr = s;
+    r.a = a;
+    r.b = bb;
+    r.pad = GLS ? (uint64_t)__double_as_longlong(w) : 0ull;
+  }
+  rec[j] = r;
+}
+
 // grid.x: object; grid.y: slices of a single large object's observations.
 template <typename YT, typename Rec, bool GLS>
 __global__ void records_kernel(const double* __restrict__ t, const YT* __restrict__ y,
@@ -260,53 +341,39 @@ __global__ void records_kernel(const double* __restrict__ t, const YT* __restric
   const int64_t lo = oi.begin + (int64_t)blockIdx.y * slice;
   int64_t hi = lo + slice;
   if (hi > oi.begin + oi.n) hi = oi.begin + oi.n;
-  for (int64_t j = lo + threadIdx.x; j < hi; j += blockDim.x) {
-    const double tp = t[j] - oi.t0;
-    const uint64_t a = frac_fixed64(f_min, tp);
-    const uint64_t bb = frac_fixed64(df, tp);
-    const double xb = (double)(int64_t)bb * 5.421010862427522e-20;  // 2^-64: cycles in [-1/2, 1/2)
-    double s, c;
-    if constexpr (sizeof(Rec) == sizeof(RecF32)) {
-      // FP32 rotation: sincospi of the fraction's leading float, corrected to
-      // first order for the remainder (|lo| < 2^-25 cycle): accurate to about
-      // one FP32 ulp without an FP64 transcendental (GB300's FP64 pipe is
-      // 1/64 of its FP32 rate).
-      const float hi = (float)xb;
-      const float lo = (float)(xb - (double)hi);
-      float sh, ch;
-      sincospif(2.0f * hi, &sh, &ch);
-      const float d = 6.28318530717958647692f * lo;
-      c = (double)fmaf(-sh, d, ch);
-      s = (double)fmaf(ch, d, sh);
-    } else {
-      sincospi(2.0 * xb, &s, &c);
+  for (int64_t j = lo + threadIdx.x; j < hi; j += blockDim.x) make_record<YT, Rec, GLS>(t, y, dy, j, oi, f_min, df, rec);
+}
+
+// One object of at most kFusedMaxNt observations in one launch: every CTA
+// computes the object's statistics itself (the same one-pass sums over all
+// observations, in the same order, so every CTA gets the same bits), CTA 0
+// stores them and clears the four work-counter words, and each CTA writes
+// the records of its slice of kStatSlice observations.
+template <typename YT, typename Rec, bool GLS>
+__global__ void __launch_bounds__(kStatSlice) single_prologue_kernel(
+    const double* __restrict__ t, const YT* __restrict__ y, const YT* __restrict__ dy, int64_t n, int center,
+    int norm, double f_min, double df, ObjInfo* __restrict__ obj, Rec* __restrict__ rec,
+    uint32_t* __restrict__ queue) {
+  __shared__ StatAcc sh[32];
+  __shared__ ObjInfo s_oi;
+  const double K = n > 0 ? (double)y[0] : 0.0;
+  StatAcc a = stat_identity();
+  stat_accumulate<YT, GLS>(t, y, dy, 0, n, K, a);
+  a = stat_block_merge<GLS>(a, sh);
+  if (threadIdx.x == 0) {
+    ObjInfo oi = stat_finish<GLS>(a, K, 0, n, 0, center);
+    stat_norm(oi, norm, GLS);
+    s_oi = oi;
+    if (blockIdx.x == 0) {
+      obj[0] = oi;
+      queue[0] = queue[1] = queue[2] = queue[3] = 0u;
     }
-    double w = 1.0;
-    if (GLS && dy) {
-      const double ej = (double)dy[j];
-      w = 1.0 / (ej * ej);
-    }
-    const double yc = (GLS ? w : 1.0) * ((double)y[j] - oi.ymean);
-    Rec r;
-    if constexpr (sizeof(Rec) == sizeof(RecF32)) {
-      r.y = (float)yc;
-      r.cr = (float)c;
-      r.sr = (float)s;
-      r.a_hi = (uint32_t)(a >> 32);
-      r.a_lo = (uint32_t)a;
-      r.b_hi = (uint32_t)(bb >> 32);
-      r.b_lo = (uint32_t)bb;
-      r.pad = GLS ? __float_as_uint((float)w) : 0u;
-    } else {
-      r.y = yc;
-      r.cr = c;
-      r.sr = s;
-      r.a = a;
-      r.b = bb;
-      r.pad = GLS ? (uint64_t)__double_as_longlong(w) : 0ull;
-    }
-    rec[j] = r;
   }
+  __syncthreads();
+  const ObjInfo oi = s_oi;
+  if (oi.flags & (LSP_FLAG_BAD_OFFSETS | LSP_FLAG_NONFINITE)) return;
+  const int64_t j = (int64_t)blockIdx.x * kStatSlice + threadIdx.x;
+  if (j < n) make_record<YT, Rec, GLS>(t, y, dy, j, oi, f_min, df, rec);
 }
 
 __global__ void hist_kernel(const ObjInfo* __restrict__ obj, int64_t n_obj, uint32_t* hist) {
@@ -343,6 +410,16 @@ __global__ void scan_kernel(uint32_t* hist) {
   }
 }
 
+// Queue position of the object with the r-th most observations: the longest
+// and the shortest alternate (r = 0, n-1, 1, n-2, ...), so the items resident
+// on an SM at any time mix long objects with short ones, whose fixed costs
+// (queue, staging and epilogue latency) the long ones' arithmetic hides; the
+// queue still ends with objects of middling length.
+__device__ __forceinline__ int64_t interleaved_pos(int64_t r, int64_t n) {
+  const int64_t half = (n + 1) / 2;
+  return r < half ? 2 * r : 2 * (n - 1 - r) + 1;
+}
+
 __global__ void scatter_kernel(const ObjInfo* __restrict__ obj, int64_t n_obj, uint32_t* start,
                                int32_t* order) {
   for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < n_obj;
@@ -350,7 +427,7 @@ __global__ void scatter_kernel(const ObjInfo* __restrict__ obj, int64_t n_obj, u
     int n = obj[o].n;
     int bin = LSP_HIST_BINS - 1 - (n < LSP_HIST_BINS - 1 ? n : LSP_HIST_BINS - 1);
     uint32_t pos = atomicAdd(&start[bin], 1u);
-    order[pos] = (int32_t)o;
+    order[interleaved_pos((int64_t)pos, n_obj)] = (int32_t)o;
   }
 }
 
@@ -432,6 +509,31 @@ cudaError_t launch_records(const double* t, const void* y, bool y64, const ObjIn
     }
   }
 #undef LSP_REC
+  return cudaGetLastError();
+}
+
+cudaError_t launch_single_prologue(const double* t, const void* y, bool y64, int64_t n, int center, int norm,
+                                   double f_min, double df, bool rec64, ObjInfo* obj, void* rec, uint32_t* queue,
+                                   cudaStream_t stream, bool gls, const void* dy) {
+  if (n < 0 || n > kFusedMaxNt) return cudaErrorInvalidValue;
+  const unsigned g = (unsigned)(n > 0 ? (n + kStatSlice - 1) / kStatSlice : 1);
+#define LSP_SP(YT, REC, G)                                                                                       \
+  single_prologue_kernel<YT, REC, G><<<g, kStatSlice, 0, stream>>>(t, (const YT*)y, (const YT*)dy, n, center, norm, \
+                                                                  f_min, df, obj, (REC*)rec, queue)
+  if (rec64) {
+    if (y64) {
+      if (gls) LSP_SP(double, RecF64, true); else LSP_SP(double, RecF64, false);
+    } else {
+      if (gls) LSP_SP(float, RecF64, true); else LSP_SP(float, RecF64, false);
+    }
+  } else {
+    if (y64) {
+      if (gls) LSP_SP(double, RecF32, true); else LSP_SP(double, RecF32, false);
+    } else {
+      if (gls) LSP_SP(float, RecF32, true); else LSP_SP(float, RecF32, false);
+    }
+  }
+#undef LSP_SP
   return cudaGetLastError();
 }
 

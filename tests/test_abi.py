@@ -213,7 +213,7 @@ int main(void) {
   F(lsp_proposer, lag_max); F(lsp_proposer, k_windows); F(lsp_proposer, stop_power);
   F(lsp_proposer, fallback_power); F(lsp_proposer, inconclusive_fallback); F(lsp_proposer, norm);
   F(lsp_config, packed); F(lsp_config, trig); F(lsp_config, staging);
-  F(lsp_trial, ms); F(lsp_trial, max_err); F(lsp_trial, passed);
+  F(lsp_trial, ms); F(lsp_trial, max_err); F(lsp_trial, passed); F(lsp_trial, worst_object);
   F(lsp_peak, power); F(lsp_peak, freq); F(lsp_peak, period); F(lsp_peak, flags);
   return 0;
 }
@@ -235,7 +235,7 @@ int main(void) {
         assert int(out["lsp_proposer." + name]) == getattr(L.Proposer, name).offset, name
     for name in ("packed", "trig", "staging"):
         assert int(out["lsp_config." + name]) == getattr(L.Config, name).offset
-    for name in ("ms", "max_err", "passed"):
+    for name in ("ms", "max_err", "passed", "worst_object"):
         assert int(out["lsp_trial." + name]) == getattr(L.Trial, name).offset
     for name in ("power", "freq", "period", "flags"):
         assert int(out["lsp_peak." + name]) == L.PEAK_DTYPE.fields[name][1]

@@ -393,3 +393,22 @@ def test_trained_network_beats_untrained(env):
     assert res["recovery"] >= 0.99 and base["recovery"] >= 0.99
     assert res["pair_fraction"] < 0.5 * base["pair_fraction"], (res, base)
     assert res["mean_windows"] < base["mean_windows"]
+
+
+def test_committed_network_meets_the_targets(env):
+    """The committed network (weights/proposer_survey.npz, trained on 1e6
+    curves by the library's own kernels) on 20000 fresh survey-shaped objects:
+    at least 99 % of the full-grid periods recovered (first maximum within one
+    bin) while evaluating under a tenth of the full grid's pairs, through the
+    one-call path."""
+    import os
+    lsp, L, torch, dev = env
+    path = os.path.join(os.path.dirname(L.__file__), "weights", "proposer_survey.npz")
+    prop, meta = L.Proposer.load_npz(path, dev)
+    assert "1000000" in meta["trained_on"]
+    s = L.labelled_set(20000, dev, "learned_infer", part=7)
+    res = L.evaluate(prop, s)
+    assert res["recovery"] >= 0.99 and res["pair_fraction"] < 0.1, res
+    pk, info = L.propose_and_refine(prop, s["t"], s["y"], s["off"], s["grid"])
+    got = lsp.peaks_to_numpy(pk)
+    assert np.mean(np.abs(got["idx"] - s["full_idx"].cpu().numpy()) <= 1) >= 0.99

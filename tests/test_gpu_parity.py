@@ -385,6 +385,52 @@ def test_autotune_keeps_parity(env, small_batch, tmp_path):
 
 
 # ------------------------------------------------------- full-size shapes
+def test_autotune_gate_checks_more_than_the_first_object(env):
+    """A benign first object (40 observations, a strong sinusoid) before a long
+    one (8000 observations: the longest FP32 sums) and an ill-conditioned one
+    (one hour per night: at twice the frequency of whole cycles per day every
+    phase aligns and N - R is small).  The gate checks all three; the error it
+    reports for each equals what the chosen configuration gives against the
+    FP64 path on the whole batch; and the largest, which decides the gate, is
+    the ill-conditioned object's, above the first object's."""
+    lsp, torch, dev = env
+    rng = np.random.default_rng(5)
+    grid = synth.Grid(0.24, 12.0, 20011)
+    t0 = np.sort(rng.uniform(60000, 60400, 40))
+    t1 = np.sort(rng.uniform(60000, 63650, 8000))
+    t2 = np.sort(60000.0 + rng.choice(3650, 300, replace=False) + rng.uniform(0, 1 / 24, 300))
+    segs = [(t0, np.sin(2 * np.pi * 1.7 * t0) + 0.01 * rng.normal(size=40)),
+            (t1, rng.normal(0, 1, 8000)),
+            (t2, np.sin(2 * np.pi * 0.3 * t2) + 0.2 * rng.normal(size=300))]
+    sv = synth.ragged_survey(9, seed=31, grid=grid)
+    for o in range(sv.n_obj):
+        sl = slice(sv.offsets[o], sv.offsets[o + 1])
+        segs.append((sv.t[sl], sv.y[sl]))
+    b = _custom_batch(segs, grid)
+    g = lsp.Grid(grid.f_min, grid.f_max, grid.n_f)
+    t = _dev(torch, dev, b.t, torch.float64)
+    y = _dev(torch, dev, b.y, torch.float32)
+    off = _dev(torch, dev, b.offsets, torch.int64)
+    plan = lsp.Plan(b.n_obj, b.t.size, g)
+    cfg, trials = plan.autotune(t, y, off, return_trials=True)
+    rep = dict(plan.gate_report())
+    assert {0, 1, 2} <= set(rep), rep  # first, longest, worst-conditioned
+    assert len(rep) <= 8
+    kw = dict(k_reseed=cfg["k_reseed"], freqs_per_thread=cfg["freqs_per_thread"], block_threads=cfg["block_threads"])
+    p32, _ = batch(env, b, "fp32", return_power=True, **kw)
+    # the FP64 path on the magnitudes the FP32 path sees (FP32, widened)
+    b32 = synth.Batch(b.t, b.y.astype(np.float32).astype(np.float64), b.offsets, b.grid, b.f_true, b.sigma)
+    p64, _ = batch(env, b32, "fp64", return_power=True)
+    for o, e in rep.items():
+        assert np.float32(np.max(np.abs(p32[o] - p64[o]))) == np.float32(e), (o, e)
+    # the ill-conditioned object, not the first one, sets the gate's error
+    assert rep[2] > rep[0] and max(rep, key=rep.get) == 2, rep
+    chosen = [tr for tr in trials if tr["passed"] and tr["config"] == cfg]
+    assert chosen and chosen[0]["max_err"] == np.float32(max(rep.values()))
+    assert chosen[0]["worst_object"] == 2
+    plan.close()
+
+
 def test_full_single_small(env):
     """One object, N_t=1000, N_f=1e5: the full periodogram against the full oracle."""
     b = synth.single_small()
