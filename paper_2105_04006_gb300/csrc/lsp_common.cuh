@@ -12,6 +12,8 @@
 //   partial  part[split * n_f]          split-N_t partial sums (single object)
 #pragma once
 
+#include <type_traits>
+
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -232,6 +234,29 @@ static __device__ __noinline__ double exact_power_warp(const RecF32* __restrict_
   return norm_scale * lsp_power<double>(xc, xs, cc, cs, (double)n, EpsRel<double>::v);
 }
 
+// The same power evaluated by one lane alone, over the observations in
+// order: for objects of at most kLaneExactMaxObs observations a warp per bin
+// would leave most lanes idle and spend more on its FP64 shuffles than on
+// the sums, so the lanes re-evaluate their own bins side by side instead.
+constexpr int kLaneExactMaxObs = 64;
+static __device__ __noinline__ double exact_power_lane(const RecF32* __restrict__ rec, int64_t begin, int n,
+                                                       uint32_t k, double norm_scale) {
+  double xc = 0.0, xs = 0.0, cc = 0.0, cs = 0.0;
+  for (int j = 0; j < n; ++j) {
+    const RecF32 r = rec[begin + j];
+    const uint64_t a = ((uint64_t)r.a_hi << 32) | r.a_lo;
+    const uint64_t b = ((uint64_t)r.b_hi << 32) | r.b_lo;
+    double c, s;
+    seed_sincos_f64(a + (uint64_t)k * b, c, s);
+    const double y = (double)r.y;
+    xc = fma(y, c, xc);
+    xs = fma(y, s, xs);
+    cc = fma(c, c, cc);
+    cs = fma(c, s, cs);
+  }
+  return norm_scale * lsp_power<double>(xc, xs, cc, cs, (double)n, EpsRel<double>::v);
+}
+
 // ---------------------------------------- generalized periodogram (Section 4.11)
 // Power of the weighted fit y ~ a cos + b sin + c from the six weighted sums
 // (y centred on its weighted mean, u = w y'):  YC = sum u c, YS = sum u s,
@@ -252,7 +277,10 @@ __device__ __forceinline__ Real gls_power(Real yc, Real ys, Real c, Real s, Real
   ill = d < Real(0.0125) * w * w;
   if (!(d > eps_rel * w * w) || !(yy > Real(0))) return Real(0);
   const Real num = ss * yc * yc + cc * ys * ys - Real(2) * cs * yc * ys;
-  return (num > Real(0) ? num : Real(0)) / (yy * d);
+  if constexpr (std::is_same<Real, float>::value)  // the SFU's fast division (relative error ~1e-7)
+    return __fdividef(num > 0.0f ? num : 0.0f, yy * d);
+  else
+    return (num > Real(0) ? num : Real(0)) / (yy * d);
 }
 
 // FP64 re-evaluation of a generalized bin by the whole warp (exact phases).
@@ -284,10 +312,49 @@ static __device__ __noinline__ double exact_gls_power_warp(const RecF32* __restr
   return norm_scale * gls_power<double>(xc, xs, c1, s1, cc, cs, wsum, yy, EpsRel<double>::v, ill);
 }
 
+// exact_gls_power_warp by one lane alone (see exact_power_lane).
+static __device__ __noinline__ double exact_gls_power_lane(const RecF32* __restrict__ rec, int64_t begin, int n,
+                                                           uint32_t k, double wsum, double yy, double norm_scale) {
+  double xc = 0.0, xs = 0.0, c1 = 0.0, s1 = 0.0, cc = 0.0, cs = 0.0;
+  for (int j = 0; j < n; ++j) {
+    const RecF32 r = rec[begin + j];
+    const uint64_t a = ((uint64_t)r.a_hi << 32) | r.a_lo;
+    const uint64_t b = ((uint64_t)r.b_hi << 32) | r.b_lo;
+    double c, s;
+    seed_sincos_f64(a + (uint64_t)k * b, c, s);
+    const double u = (double)r.y, w = (double)__uint_as_float(r.pad);
+    xc = fma(u, c, xc);
+    xs = fma(u, s, xs);
+    c1 = fma(w, c, c1);
+    s1 = fma(w, s, s1);
+    cc = fma(w * c, c, cc);
+    cs = fma(w * c, s, cs);
+  }
+  bool ill;
+  return norm_scale * gls_power<double>(xc, xs, c1, s1, cc, cs, wsum, yy, EpsRel<double>::v, ill);
+}
+
 template <int F>
 __device__ __forceinline__ void fix_ill_conditioned_gls(float (&pv)[F], uint32_t bad, uint32_t k0,
                                                         const RecF32* __restrict__ rec, const ObjInfo& oi) {
   if (!__any_sync(0xffffffffu, bad != 0u)) return;
+  if (oi.n <= kLaneExactMaxObs) {
+    // a short object: each lane re-evaluates its own flagged bins, lowest
+    // first, one per round, so every lane with a bin left works in each
+    // round (the rounds: the most bins any lane flagged)
+    while (__any_sync(0xffffffffu, bad != 0u)) {
+      if (bad) {
+        const int m = __ffs(bad) - 1;
+        bad &= bad - 1u;
+        const float p = (float)exact_gls_power_lane(rec, oi.begin, oi.n, k0 + (uint32_t)m, oi.wsum, oi.sum_y2,
+                                                    oi.norm_scale);
+#pragma unroll
+        for (int mm = 0; mm < F; ++mm)
+          if (mm == m) pv[mm] = p;
+      }
+    }
+    return;
+  }
   const int lane = threadIdx.x & 31;
 #pragma unroll
   for (int m = 0; m < F; ++m) {
@@ -309,6 +376,19 @@ __device__ __forceinline__ void fix_ill_conditioned(float (&pv)[F], uint32_t bad
                                                     const RecF32* __restrict__ rec, int64_t begin,
                                                     int n, double norm_scale) {
   if (!__any_sync(0xffffffffu, bad != 0u)) return;
+  if (n <= kLaneExactMaxObs) {  // a short object: lanes in rounds, as in fix_ill_conditioned_gls
+    while (__any_sync(0xffffffffu, bad != 0u)) {
+      if (bad) {
+        const int m = __ffs(bad) - 1;
+        bad &= bad - 1u;
+        const float p = (float)exact_power_lane(rec, begin, n, k0 + (uint32_t)m, norm_scale);
+#pragma unroll
+        for (int mm = 0; mm < F; ++mm)
+          if (mm == m) pv[mm] = p;
+      }
+    }
+    return;
+  }
   const int lane = threadIdx.x & 31;
 #pragma unroll
   for (int m = 0; m < F; ++m) {
