@@ -551,6 +551,20 @@ lsp_status lsp_window_labels(const lsp_peak* peaks, int64_t n_obj, int64_t strid
 lsp_status lsp_probe_fma_rates(double* f32_per_s, double* f32x2_per_s, double* f64_per_s,
                                lsp_stream_t stream);
 
+/*
+ * Accuracy probe of the FP64 path's sin/cos of a fixed-point phase (no
+ * counterpart in the paper): the library evaluates (cos, sin)(2 pi phi) for
+ * a 64-bit phase phi = frac in units of 2^-64 cycle from a 256-entry table of
+ * e^{2 pi i j / 256} and a short Taylor series of the remaining angle
+ * (< 2 pi / 256), rotated together.  The probe draws n phases on the device
+ * (the table points and their neighbours, then splitmix64 of seed + i),
+ * evaluates each both that way and with CUDA's sincospi, and writes the
+ * largest absolute difference of either component to *max_abs_err (host
+ * pointer).  Synchronises `stream`; allocates and frees one device word.
+ * Errors: LSP_E_ARG for n < 1 or a NULL output, LSP_E_CUDA.
+ */
+lsp_status lsp_probe_sincos_fixed64(int64_t n, uint64_t seed, double* max_abs_err, lsp_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -93,7 +93,7 @@ EXPORTS = [
     "lsp_refine_windows", "lsp_batch_gls", "lsp_periodogram_gls", "lsp_workspace_size_gls",
     "lsp_probe_fma_rates", "lsp_plan_autotune_ex", "lsp_plan_set_host_parts", "lsp_plan_get_host_parts",
     "lsp_propose_refine", "lsp_propose_refine_workspace_size", "lsp_window_labels", "lsp_noalloc_prepare",
-    "lsp_plan_gate_report",
+    "lsp_plan_gate_report", "lsp_probe_sincos_fixed64",
 ]
 
 
@@ -167,6 +167,7 @@ def lib():
             L.lsp_window_labels.argtypes = [P, i64, i64, i32, P, P]
             L.lsp_noalloc_prepare.argtypes = []
             L.lsp_plan_gate_report.argtypes = [P, P, P, i32, ctypes.POINTER(i32)]
+            L.lsp_probe_sincos_fixed64.argtypes = [i64, ctypes.c_uint64, ctypes.POINTER(ctypes.c_double), P]
             L.lsp_plan_destroy.argtypes = [P]
             L.lsp_plan_destroy.restype = None
             for name in EXPORTS:

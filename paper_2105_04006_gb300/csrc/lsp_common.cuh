@@ -149,11 +149,31 @@ __device__ __forceinline__ void seed_sincos_f32(uint32_t ph, float& c, float& s)
   __sincosf(x, &s, &c);
 }
 
-// (cos, sin) of a 64-bit fixed-point phase in FP64 (accurate library sincospi).
-__device__ __forceinline__ void seed_sincos_f64(uint64_t ph, double& c, double& s) {
-  double x = (double)(int64_t)ph * 5.421010862427522e-20;  // 2^-64: cycles in [-1/2, 1/2)
-  sincospi(2.0 * x, &s, &c);
+// (cos, sin) of a 64-bit fixed-point phase (2^64 = one cycle) in FP64,
+// without a library call.  The phase's top 8 bits pick e^{2 pi i j / 256}
+// from a table (correctly rounded, lsp_twiddles.inc); the remaining 56 bits
+// are an angle x < 2 pi / 256 = 0.0245 rad whose cosine and sine come from
+// their Taylor series, 1 - x^2/2 + x^4/24 - x^6/720 and x - x^3/6 + x^5/120 -
+// x^7/5040 (the first omitted terms, x^8/8! and x^9/9!, are below 4e-18);
+// the two are combined by the angle-addition formulas.  About a dozen FP64
+// operations against a library sincos's few dozen, at an error of a few
+// 1e-16 (checked against sincospi by lsp_probe_sincos_fixed64).
+__device__ const double2 kTwiddle256[256] = {
+#include "lsp_twiddles.inc"
+};
+
+__device__ __forceinline__ void sincos_fixed64(uint64_t ph, double& c, double& s) {
+  const double2 t = __ldg(&kTwiddle256[ph >> 56]);
+  const double x = (double)(ph & 0x00FFFFFFFFFFFFFFull) * 3.4061215800865545e-19;  // 2 pi / 2^64
+  const double x2 = x * x;
+  const double cx = fma(x2, fma(x2, fma(x2, -1.0 / 720.0, 1.0 / 24.0), -0.5), 1.0);
+  const double sx = fma(x * x2, fma(x2, fma(x2, -1.0 / 5040.0, 1.0 / 120.0), -1.0 / 6.0), x);
+  c = fma(t.x, cx, -(t.y * sx));
+  s = fma(t.y, cx, t.x * sx);
 }
+
+// (cos, sin) of a 64-bit fixed-point phase in FP64.
+__device__ __forceinline__ void seed_sincos_f64(uint64_t ph, double& c, double& s) { sincos_fixed64(ph, c, s); }
 
 // --------------------------------------------------------- power (Eq. 1-2)
 // Eq. 2 evaluated from single-scan sums (the refactoring of Section 2):

@@ -113,3 +113,75 @@ extern "C" lsp_status lsp_probe_fma_rates(double* f32_per_s, double* f32x2_per_s
   if (f64_per_s) *f64_per_s = r64;
   return LSP_OK;
 }
+
+// ------------------------------------------------------------------------
+// Accuracy probe of sincos_fixed64 (the FP64 seeds' sin/cos): n phases from a
+// counter-based hash (splitmix64 of seed + i, so every bit pattern can occur,
+// plus the 256 table points and their neighbours), each evaluated both ways;
+// the largest |difference| of cos and of sin against CUDA's sincospi.
+namespace {
+
+__device__ __forceinline__ uint64_t splitmix64(uint64_t z) {
+  z += 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+__global__ void probe_sincos_kernel(int64_t n, uint64_t seed, unsigned long long* max_bits) {
+  __shared__ unsigned long long sh[32];
+  double worst = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    uint64_t ph;
+    if (i < 768) {  // the table points and their neighbours
+      ph = ((uint64_t)(i / 3) << 56) + (uint64_t)(i % 3) - 1ull;
+    } else {
+      ph = splitmix64(seed + (uint64_t)i);
+    }
+    double c, s, cr, sr;
+    lsp::sincos_fixed64(ph, c, s);
+    const double x = (double)(int64_t)ph * 5.421010862427522e-20;  // cycles in [-1/2, 1/2)
+    sincospi(2.0 * x, &sr, &cr);
+    worst = fmax(worst, fmax(fabs(c - cr), fabs(s - sr)));
+  }
+  unsigned long long m = (unsigned long long)__double_as_longlong(worst);
+  for (int off = 16; off > 0; off >>= 1) {
+    const unsigned long long o = __shfl_xor_sync(0xffffffffu, m, off);
+    m = o > m ? o : m;
+  }
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = sh[w] > m ? sh[w] : m;
+    atomicMax(max_bits, m);
+  }
+}
+
+}  // namespace
+
+extern "C" lsp_status lsp_probe_sincos_fixed64(int64_t n, uint64_t seed, double* max_abs_err, lsp_stream_t stream_) {
+  cudaStream_t stream = (cudaStream_t)stream_;
+  if (n < 1 || !max_abs_err) {
+    lsp::set_last_error("lsp_probe_sincos_fixed64: n must be >= 1 and max_abs_err not NULL");
+    return LSP_E_ARG;
+  }
+  unsigned long long* d = nullptr;
+  unsigned long long h = 0ull;
+  cudaError_t e = cudaMalloc(&d, sizeof h);
+  if (e == cudaSuccess) e = cudaMemsetAsync(d, 0, sizeof h, stream);
+  if (e == cudaSuccess) {
+    probe_sincos_kernel<<<1024, 256, 0, stream>>>(n, seed, d);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&h, d, sizeof h, cudaMemcpyDeviceToHost, stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+  if (d) cudaFree(d);
+  if (e != cudaSuccess) {
+    char msg[160];
+    snprintf(msg, sizeof msg, "lsp_probe_sincos_fixed64: %s", cudaGetErrorString(e));
+    lsp::set_last_error(msg);
+    return LSP_E_CUDA;
+  }
+  *max_abs_err = __builtin_bit_cast(double, h);
+  return LSP_OK;
+}

@@ -671,6 +671,18 @@ def test_host_group_count_rule(env, small_batch):
     one.close()
 
 
+def test_fixed_point_sincos_matches_cuda(env):
+    """The FP64 seeds' sin/cos (256-entry table of e^{2 pi i j/256} plus a
+    Taylor series of the remaining angle) against CUDA's sincospi on 4e6
+    phases, the table points and their neighbours included: within a few FP64
+    ulp of 1."""
+    lsp, torch, dev = env
+    import ctypes
+    err = ctypes.c_double(-1.0)
+    assert lsp.lib().lsp_probe_sincos_fixed64(4_000_000, 12345, ctypes.byref(err), None) == 0
+    assert 0.0 <= err.value <= 1e-15, err.value
+
+
 def test_fma_rate_probe_is_plausible(env):
     # ceilings for the roofline fractions: below the nominal unit counts at the
     # highest SM clock of the part (2.07 GHz), and not far below them
