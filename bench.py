@@ -832,6 +832,7 @@ def run_gpu(args, w, name):
           if w["power"] else None)
     pk_host = np.empty(b.n_obj * w["top_k"], dtype=lsp.PEAK_DTYPE)
     plan.enable_timing(False)
+    plan.set_host_parts(args.host_parts)
     plan.execute_host(th, yh, oh, power=ph, peaks=pk_host)  # warm: allocates staging, captures
     barrier()
     e2e_ms = []
@@ -923,6 +924,7 @@ def run_gpu(args, w, name):
             "parity_vs_oracle": parity,
             "e2e": {"value": e2e_value, "unit": "objects/s", "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(d2h), "ms_per_step": statistics.mean(e2e_ms),
+                    "host_parts": plan.host_parts(power=ph is not None),
                     "ms_min": min(e2e_ms), "ms_max": max(e2e_ms), "clocks": clocks_e2e},
             "gpu_launches": plan.kernel_count * args.steps,
             "clocks": clocks,
@@ -1008,6 +1010,8 @@ def main():
     ap.add_argument("--ablations", action="store_true",
                     help="time every autotuner candidate, including the trig/staging ablation kernels, and print "
                          "them (one JSON line) instead of the benchmark")
+    ap.add_argument("--host-parts", type=int, default=0,
+                    help="object groups of the e2e leg's host entry point (0: the library's rule, 1: one pass)")
     ap.add_argument("--n-obj", type=int, default=None,
                     help="objects in a batch workload (default: the workload's own count)")
     args = ap.parse_args()

@@ -291,27 +291,34 @@ lsp_status lsp_plan_execute_host(lsp_plan* plan, const double* t, const void* y,
                                  lsp_stream_t stream);
 
 /*
- * How lsp_plan_execute_host returns the periodogram of a batch (the overlap
- * of host transfers with computation, Section 3.5).  parts = 1: one pass, as
+ * How lsp_plan_execute_host runs a batch in object groups (the overlap of
+ * host transfers with computation, Section 3.5).  parts = 1: one pass, as
  * described above.  parts >= 2: the objects are cut into `parts` contiguous
- * groups of (nearly) equal count, each run as a batch of its own into its rows
- * of a device buffer, and each group's rows are copied to power_out on a
- * second stream while the following groups compute; the copies always come
- * from the device buffer, also for page-locked power_out.  Powers and peaks
- * equal those of one pass bit for bit.  parts = 0 (the default): 8 groups
- * for periodograms of at least 256 MiB, else one pass.  The count is clamped
- * to n_obj / 2 (every group has two objects or more; a one-object plan always
- * runs in one pass).  Without power_out the setting has no effect, and
- * offsets that are not monotonic inside [0, total_nt] take the one-pass route
- * (which flags the objects they touch).
+ * groups, each run as a batch of its own once its observations have been
+ * copied in on a second stream, so that the next group's copy overlaps this
+ * group's kernels.  With power_out the groups have (nearly) equal object
+ * counts and run into their rows of a device buffer, and a third stream
+ * copies each group's rows to power_out while the following groups compute
+ * (the copies always come from the device buffer, also for page-locked
+ * power_out).  Without power_out the groups' observation counts grow
+ * four-fold (1 : 4 : 16 : ...), so that only the first, smallest group's
+ * input copy is exposed (more than 16 groups, or boundaries that would leave
+ * a group with fewer than two objects, fall back to equal counts).  Powers
+ * and peaks equal those of one pass bit for bit.  parts = 0 (the default): 8
+ * groups for periodograms of at least 256 MiB, else 4 for inputs (t and y)
+ * of at least 64 MiB, else one pass.  The count is clamped to n_obj / 2
+ * (every group has two objects or more; a one-object plan always runs in one
+ * pass).  Offsets that are not monotonic inside [0, total_nt] take the
+ * one-pass route (which flags the objects they touch).
  * Errors: LSP_E_ARG for a NULL plan or parts < 0.
  */
 lsp_status lsp_plan_set_host_parts(lsp_plan* plan, int32_t parts);
 
 /*
- * The group count lsp_plan_execute_host uses for a periodogram of
- * power_bytes bytes (n_obj * n_f * 4 for FP32 plans, * 8 for FP64), after
- * the default rule and the clamp above.  Host only.
+ * The group count lsp_plan_execute_host uses for a call that returns
+ * power_bytes bytes of periodogram (n_obj * n_f * 4 for FP32 plans, * 8 for
+ * FP64; 0 for a call that returns peaks only), after the default rule and
+ * the clamp above.  Host only.
  */
 lsp_status lsp_plan_get_host_parts(const lsp_plan* plan, int64_t power_bytes, int32_t* parts);
 

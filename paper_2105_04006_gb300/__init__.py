@@ -437,14 +437,15 @@ class Plan:
         return int(v.value)
 
     def set_host_parts(self, parts: int):
-        """Object groups of execute_host's periodogram return (0: by size, 1: one
-        pass, n: n groups whose copies overlap the next groups' computation)."""
+        """Object groups of execute_host (0: by size, 1: one pass, n: n groups
+        whose input and periodogram copies overlap the other groups' kernels)."""
         _check(lib().lsp_plan_set_host_parts(self._h, int(parts)))
 
-    def host_parts(self) -> int:
-        """The group count execute_host uses for this plan's full periodogram."""
+    def host_parts(self, power: bool = True) -> int:
+        """The group count execute_host uses for a call that returns this plan's
+        full periodogram (power=True) or peaks only (power=False)."""
         v = ctypes.c_int32()
-        nbytes = self.n_obj * self.grid.n_f * (8 if self.opts.precision == FP64 else 4)
+        nbytes = self.n_obj * self.grid.n_f * (8 if self.opts.precision == FP64 else 4) if power else 0
         _check(lib().lsp_plan_get_host_parts(self._h, nbytes, ctypes.byref(v)))
         return int(v.value)
 

@@ -474,6 +474,10 @@ struct lsp_plan {
   cudaStream_t copy_stream = nullptr;
   std::vector<cudaEvent_t> part_ev;
   cudaEvent_t copy_done = nullptr;
+  // input streaming: each group's observations are copied on in_stream
+  cudaStream_t in_stream = nullptr;
+  std::vector<cudaEvent_t> in_ev;
+  cudaEvent_t start_ev = nullptr;
   // the last autotune's error gate: objects and the chosen configuration's errors
   std::vector<int64_t> gate_obj;
   std::vector<double> gate_err;
@@ -603,32 +607,68 @@ void cache_store(const char* path, const std::string& key, const lsp_config& c, 
     << "}\n";
 }
 
-// Number of object groups of the host entry point's periodogram return.
-int host_parts_for(const lsp_plan* p, size_t pbytes) {
+// Number of object groups of the host entry point (power_bytes: the size of
+// the periodogram it returns, 0 for peaks only).
+int host_parts_for(const lsp_plan* p, size_t power_bytes) {
   int parts = p->host_parts;
-  if (parts == 0) parts = pbytes >= ((size_t)256 << 20) ? 8 : 1;
+  if (parts == 0) {
+    const size_t in_bytes = (size_t)p->total_nt * (p->opts.precision == LSP_FP64 ? 16 : 12);
+    parts = power_bytes >= ((size_t)256 << 20) ? 8 : in_bytes >= ((size_t)64 << 20) ? 4 : 1;
+  }
   const int64_t most = p->n_obj / 2;  // every group a batch of >= 2 objects
   if (parts > most) parts = (int)most;
   return parts < 1 ? 1 : parts;
 }
 
-// The periodogram return in `parts` contiguous object groups (the overlap of
-// transfers with computation of Section 3.5): each group runs as a batch of its
-// own into its rows of the device power buffer on `s`, and a second stream
-// copies those rows to power_out while the next group computes.  An object's
-// powers and peaks do not depend on the other objects of its batch, so the
-// results equal those of one pass bit for bit.  The groups share the plan's
-// workspace, which only kernels on `s` touch.
-lsp_status execute_host_parts(lsp_plan* p, int parts, const int64_t* offsets, void* power_out,
-                              bool want_peaks, cudaStream_t s) {
+// Group boundaries first[0..parts] (objects).  With a periodogram to return,
+// groups of (nearly) equal object counts: each group's rows leave while the
+// next group computes, and the last group's copy is the exposed one.  Without
+// one, the groups' observation counts grow four-fold (1 : 4 : 16 : ...): a
+// group's inputs arrive while the previous group computes, so only the first,
+// smallest group's copy is exposed.  Offsets are monotonic here; more than 16
+// groups, or a boundary that would leave a group under two objects, fall back
+// to equal counts.
+void host_group_bounds(const lsp_plan* p, int parts, const int64_t* offsets, bool by_count,
+                       std::vector<int64_t>& first) {
+  const int64_t n = p->n_obj;
+  first.assign((size_t)parts + 1, 0);
+  for (int j = 0; j <= parts; ++j) first[(size_t)j] = n * j / parts;
+  if (by_count || parts > 16) return;
+  std::vector<int64_t> g((size_t)parts + 1, 0);
+  const double nt = (double)(offsets[n] - offsets[0]);
+  double w = 1.0, cum = 0.0, all = 0.0;
+  for (int j = 0; j < parts; ++j, w *= 4.0) all += w;
+  w = 1.0;
+  g[(size_t)parts] = n;
+  for (int j = 1; j < parts; ++j, w *= 4.0) {
+    cum += w;
+    const int64_t target = offsets[0] + (int64_t)(nt * (cum / all));
+    g[(size_t)j] = std::lower_bound(offsets, offsets + n + 1, target) - offsets;
+  }
+  for (int j = 0; j < parts; ++j)
+    if (g[(size_t)j + 1] - g[(size_t)j] < 2) return;
+  first.swap(g);
+}
+
+// The host entry point in `parts` contiguous object groups (the overlap of
+// transfers with computation of Section 3.5).  Each group's observations are
+// copied on a second stream, and the group runs as a batch of its own on `s`
+// once they have arrived, while the next group's copy proceeds; with a
+// periodogram to return, a third stream copies each group's rows of the
+// device power buffer to power_out while the next group computes.  An
+// object's powers and peaks do not depend on the other objects of its batch,
+// so the results equal those of one pass bit for bit.  The groups share the
+// plan's workspace, which only kernels on `s` touch.
+lsp_status execute_host_parts(lsp_plan* p, int parts, const double* t, const void* y, const int64_t* offsets,
+                              void* power_out, bool want_peaks, cudaStream_t s) {
   const Layout& F = p->L;
   const size_t ysz = F.prec == LSP_FP64 ? 8 : 4;
   const size_t row = (size_t)F.n_f * ysz;
   std::vector<Layout> G((size_t)parts);
-  std::vector<int64_t> first((size_t)parts + 1);
+  std::vector<int64_t> first;
+  host_group_bounds(p, parts, offsets, power_out != nullptr, first);
   size_t ws_need = 0;
   p->h_rel.assign((size_t)(p->n_obj + parts), 0);
-  for (int j = 0; j <= parts; ++j) first[(size_t)j] = p->n_obj * j / parts;
   for (int j = 0; j < parts; ++j) {
     const int64_t a = first[(size_t)j], b = first[(size_t)j + 1];
     for (int64_t i = a; i <= b; ++i) p->h_rel[(size_t)(i + j)] = offsets[i] - offsets[a];
@@ -651,31 +691,57 @@ lsp_status execute_host_parts(lsp_plan* p, int parts, const int64_t* offsets, vo
   }
   if (!p->copy_stream)
     LSP_CUDA(cudaStreamCreateWithFlags(&p->copy_stream, cudaStreamNonBlocking), "copy stream");
+  if (!p->in_stream) LSP_CUDA(cudaStreamCreateWithFlags(&p->in_stream, cudaStreamNonBlocking), "input stream");
   if (!p->copy_done) LSP_CUDA(cudaEventCreateWithFlags(&p->copy_done, cudaEventDisableTiming), "event");
+  if (!p->start_ev) LSP_CUDA(cudaEventCreateWithFlags(&p->start_ev, cudaEventDisableTiming), "event");
   while (p->part_ev.size() < (size_t)parts) {
     cudaEvent_t e;
     LSP_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "event");
     p->part_ev.push_back(e);
   }
+  while (p->in_ev.size() < (size_t)parts) {
+    cudaEvent_t e;
+    LSP_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "event");
+    p->in_ev.push_back(e);
+  }
   LSP_CUDA(cudaMemcpyAsync(p->d_rel, p->h_rel.data(), rel_bytes, cudaMemcpyHostToDevice, s), "H2D group offsets");
-  // every group's kernels first, then the copies: a copy into pageable memory
-  // may hold the calling thread until it ends
+  // the input copies come after the work enqueued on `s` before this call
+  LSP_CUDA(cudaEventRecord(p->start_ev, s), "start event");
+  LSP_CUDA(cudaStreamWaitEvent(p->in_stream, p->start_ev, 0), "input wait");
+  // each group's copy, then its kernels: a copy from pageable memory holds the
+  // calling thread while it stages, so enqueued in this order it still
+  // overlaps the previous group's kernels
   for (int j = 0; j < parts; ++j) {
-    const int64_t a = first[(size_t)j];
-    st = run(G[(size_t)j], p->d_t + offsets[a], (const char*)p->d_y + offsets[a] * ysz, p->d_rel + a + j,
-             (char*)p->d_power + a * row, want_peaks ? p->d_peaks + a * p->opts.top_k : nullptr, p->ws, s);
+    const int64_t a = first[(size_t)j], b = first[(size_t)j + 1];
+    const int64_t o = offsets[a], m = offsets[b] - offsets[a];
+    if (m > 0) {
+      LSP_CUDA(cudaMemcpyAsync(p->d_t + o, t + o, (size_t)m * sizeof(double), cudaMemcpyHostToDevice,
+                               p->in_stream), "H2D t group");
+      LSP_CUDA(cudaMemcpyAsync((char*)p->d_y + o * ysz, (const char*)y + o * ysz, (size_t)m * ysz,
+                               cudaMemcpyHostToDevice, p->in_stream), "H2D y group");
+    }
+    LSP_CUDA(cudaEventRecord(p->in_ev[(size_t)j], p->in_stream), "input event");
+    LSP_CUDA(cudaStreamWaitEvent(s, p->in_ev[(size_t)j], 0), "group wait");
+    st = run(G[(size_t)j], p->d_t + o, (const char*)p->d_y + o * ysz, p->d_rel + a + j,
+             power_out ? (char*)p->d_power + a * row : nullptr,
+             want_peaks ? p->d_peaks + a * p->opts.top_k : nullptr, p->ws, s);
     if (st) return st;
     LSP_CUDA(cudaEventRecord(p->part_ev[(size_t)j], s), "group event");
   }
-  for (int j = 0; j < parts; ++j) {
-    const int64_t a = first[(size_t)j], b = first[(size_t)j + 1];
-    LSP_CUDA(cudaStreamWaitEvent(p->copy_stream, p->part_ev[(size_t)j], 0), "copy wait");
-    LSP_CUDA(cudaMemcpyAsync((char*)power_out + a * row, (const char*)p->d_power + a * row, (b - a) * row,
-                             cudaMemcpyDeviceToHost, p->copy_stream),
-             "D2H power group");
+  if (power_out) {
+    // the copies after every group's kernels: a copy into pageable memory
+    // may hold the calling thread until it ends
+    for (int j = 0; j < parts; ++j) {
+      const int64_t a = first[(size_t)j], b = first[(size_t)j + 1];
+      LSP_CUDA(cudaStreamWaitEvent(p->copy_stream, p->part_ev[(size_t)j], 0), "copy wait");
+      LSP_CUDA(cudaMemcpyAsync((char*)power_out + a * row, (const char*)p->d_power + a * row, (b - a) * row,
+                               cudaMemcpyDeviceToHost, p->copy_stream),
+               "D2H power group");
+    }
+    LSP_CUDA(cudaEventRecord(p->copy_done, p->copy_stream), "copy event");
+    LSP_CUDA(cudaStreamWaitEvent(s, p->copy_done, 0), "join copies");
   }
-  LSP_CUDA(cudaEventRecord(p->copy_done, p->copy_stream), "copy event");
-  LSP_CUDA(cudaStreamWaitEvent(s, p->copy_done, 0), "join copies");
+  // the input stream rejoins `s` (its last event is already waited on)
   return LSP_OK;
 }
 
@@ -727,8 +793,11 @@ void lsp_plan_destroy(lsp_plan* p) {
   cudaFree(p->d_power);
   cudaFree(p->d_rel);
   for (cudaEvent_t e : p->part_ev) cudaEventDestroy(e);
+  for (cudaEvent_t e : p->in_ev) cudaEventDestroy(e);
   if (p->copy_done) cudaEventDestroy(p->copy_done);
+  if (p->start_ev) cudaEventDestroy(p->start_ev);
   if (p->copy_stream) cudaStreamDestroy(p->copy_stream);
+  if (p->in_stream) cudaStreamDestroy(p->in_stream);
   delete p;
 }
 
@@ -858,7 +927,7 @@ static lsp_status execute_host_impl(lsp_plan* p, const double* t, const void* y,
       power_direct = attr.devicePointer;
     cudaGetLastError();
   }
-  int parts = power_out ? host_parts_for(p, pbytes) : 1;
+  int parts = host_parts_for(p, power_out ? pbytes : 0);
   if (parts > 1) {
     // groups index t and y by the offsets: they need monotonic offsets inside
     // the inputs (others take the one-pass route, which flags the objects)
@@ -868,16 +937,16 @@ static lsp_status execute_host_impl(lsp_plan* p, const double* t, const void* y,
   }
   if (parts > 1) power_direct = nullptr;
   if (power_out && !power_direct && (st = alloc(&p->d_power, pbytes))) return st;
-  LSP_CUDA(cudaMemcpyAsync(p->d_t, t, p->total_nt * sizeof(double), cudaMemcpyHostToDevice, s), "H2D t");
-  LSP_CUDA(cudaMemcpyAsync(p->d_y, y, p->total_nt * ysz, cudaMemcpyHostToDevice, s), "H2D y");
   if (parts > 1) {
-    if ((st = execute_host_parts(p, parts, offsets, power_out, peaks != nullptr, s))) return st;
+    if ((st = execute_host_parts(p, parts, t, y, offsets, power_out, peaks != nullptr, s))) return st;
     if (peaks)
       LSP_CUDA(cudaMemcpyAsync(peaks, p->d_peaks, n_peaks * sizeof(lsp_peak), cudaMemcpyDeviceToHost, s),
                "D2H peaks");
     LSP_CUDA(cudaStreamSynchronize(s), "synchronize");
     return LSP_OK;
   }
+  LSP_CUDA(cudaMemcpyAsync(p->d_t, t, p->total_nt * sizeof(double), cudaMemcpyHostToDevice, s), "H2D t");
+  LSP_CUDA(cudaMemcpyAsync(p->d_y, y, p->total_nt * ysz, cudaMemcpyHostToDevice, s), "H2D y");
   const int64_t* d_off = nullptr;
   if (offsets) {
     LSP_CUDA(cudaMemcpyAsync(p->d_off, offsets, (p->n_obj + 1) * sizeof(int64_t),
@@ -906,6 +975,7 @@ lsp_status lsp_plan_execute_host(lsp_plan* p, const double* t, const void* y,
     // host buffers: let them end before the error is reported
     cudaStreamSynchronize((cudaStream_t)stream);
     if (p->copy_stream) cudaStreamSynchronize(p->copy_stream);
+    if (p->in_stream) cudaStreamSynchronize(p->in_stream);
     cudaGetLastError();
   }
   return st;

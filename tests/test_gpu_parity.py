@@ -660,8 +660,10 @@ def test_host_group_count_rule(env, small_batch):
     v = ctypes.c_int32()
     assert lsp.lib().lsp_plan_get_host_parts(plan._h, 256 << 20, ctypes.byref(v)) == 0
     assert v.value == 8
+    assert plan.host_parts(power=False) == 1  # inputs under 64 MiB: one pass
     plan.set_host_parts(100)
     assert plan.host_parts() == b.n_obj // 2
+    assert plan.host_parts(power=False) == b.n_obj // 2
     with pytest.raises(lsp.LSPError):
         plan.set_host_parts(-1)
     plan.close()
@@ -669,6 +671,45 @@ def test_host_group_count_rule(env, small_batch):
     one.set_host_parts(4)
     assert one.host_parts() == 1
     one.close()
+    big = lsp.Plan(1000, 6_000_000, g)  # 72 MB of FP32 inputs: streamed in 4 groups
+    assert big.host_parts(power=False) == 4
+    big.close()
+
+
+@pytest.mark.parametrize("parts", [2, 4, 7])
+def test_peaks_only_host_call_streams_inputs_in_groups(env, parts):
+    """The host entry point without a periodogram streams its inputs in object
+    groups whose observation counts grow four-fold (each group's copy overlaps
+    the previous group's kernels, Section 3.5): the peaks equal the device
+    path's bit for bit, from pageable and page-locked inputs that start past
+    offset 0.  The staging buffers hold other data before each grouped call,
+    so a range that a group failed to copy would show."""
+    lsp, torch, dev = env
+    b = synth.ragged_lognormal(600, seed=31, grid=synth.Grid(0.24, 12.0, 3001))
+    pad = 5
+    t = np.concatenate([np.linspace(1.0, 2.0, pad), b.t])
+    y = np.concatenate([np.ones(pad, np.float32), b.y.astype(np.float32)])
+    off = b.offsets + pad
+    g = lsp.Grid(b.grid.f_min, b.grid.f_max, b.grid.n_f)
+    plan = lsp.Plan(b.n_obj, t.size, g, top_k=3)
+    td = _dev(torch, dev, t, torch.float64)
+    yd = _dev(torch, dev, y, torch.float32)
+    od = _dev(torch, dev, off, torch.int64)
+    pk_dev = plan.peaks_buffer(dev)
+    plan.execute(td, yd, od, peaks=pk_dev)
+    torch.cuda.synchronize()
+    want = lsp.peaks_to_numpy(pk_dev)
+    pinned = (torch.from_numpy(t).pin_memory(), torch.from_numpy(y).pin_memory(),
+              torch.from_numpy(off).pin_memory())
+    for inputs in ((t, y, off), pinned):
+        plan.set_host_parts(1)
+        plan.execute_host(t + 0.37, np.roll(y, 7), off)  # other data into the staging buffers
+        plan.set_host_parts(parts)
+        assert plan.host_parts(power=False) == parts
+        got = plan.execute_host(*inputs)
+        for name in lsp.PEAK_DTYPE.names:
+            np.testing.assert_array_equal(got[name], want[name], err_msg=name)
+    plan.close()
 
 
 def test_fixed_point_sincos_matches_cuda(env):
