@@ -578,10 +578,198 @@ __device__ __forceinline__ unsigned long long block_max_key(unsigned long long v
 }
 
 // FP32 counterpart of chunk_results: first maximum and (with cand) the top-3
-// interior local maxima and edge bins of the chunk.  `pw` is a shared buffer
-// of blockDim.x * NP floats (top-k only).
+// interior local maxima and edge bins of the chunk.  Thread t holds the NP
+// bins from chunk index t NP (k0 = k_chunk0 + t NP).  `pw` is a shared
+// buffer of at least 4 (blockDim.x / 32) + 2 floats and `red` of 32 keys.
+//
+// The top-k path keeps the chunk in registers.  Each thread tests its own
+// bins for interior local maxima (neighbours in registers, the adjacent
+// lanes' by shuffle) and keeps the best of them; a warp takes its three best
+// in three rounds of a warp-wide maximum, the winning lane re-scanning its
+// bins without the taken one; the two bins at each boundary between warps
+// are tested by warp 0 from the first and last two bins each warp publishes,
+// and warp 0 merges the warps' lists.  The chunk's first maximum is the best
+// of its first bin, its best interior local maximum and its last bin (an
+// interior first maximum is a local maximum: its left neighbour is lower,
+// its right one not higher).  Ties go to the lower bin throughout: lanes
+// and bins are scanned in increasing order with strict comparisons.  One
+// barrier; on return only warp 0 may still read the shared buffers, and the
+// callers pass a barrier before writing them again.
 template <int NP>
 __device__ void chunk_results_f32(const float (&pv)[NP], uint32_t k0, int64_t k_chunk0, int64_t n_f,
+                                  ChunkBest* best_out, ChunkCand* cand_out, float* pw,
+                                  unsigned long long* red) {
+  static_assert(NP >= 1 && NP <= 32, "bins per thread");
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  const int chunk_len = blockDim.x * NP;
+  const int64_t nvalid64 = n_f - k_chunk0;
+  const int nvalid = nvalid64 < chunk_len ? (int)nvalid64 : chunk_len;
+  const int base = tid * NP;
+  if (cand_out == nullptr) {
+    const int nv = nvalid - base;  // this thread's bins inside the grid (may be <= 0)
+    float bp = -1.0f;              // powers are >= 0: the first valid bin always enters
+    int bm = -1;
+#pragma unroll
+    for (int m = 0; m < NP; ++m)
+      if (m < nv && pv[m] > bp) {
+        bp = pv[m];
+        bm = m;
+      }
+    unsigned long long best = bm >= 0 ? pkey(bp, k0 + (uint32_t)bm) : 0ull;
+    best = block_max_key(best, red);
+    if (tid == 0) *best_out = ChunkBest{(double)key_power(best), key_index(best)};
+    return;
+  }
+  // interior local maxima among this thread's bins; a warp's first and last
+  // bins are left to warp 0 (or are the chunk's edges)
+  const int lo = lane == 0 ? 1 : 0;
+  const int hi_w = lane == 31 ? NP - 2 : NP - 1;
+  const int hi_v = nvalid - 2 - base;
+  const int hi = hi_w < hi_v ? hi_w : hi_v;
+  const float left_in = __shfl_up_sync(0xffffffffu, pv[NP - 1], 1);
+  const float right_in = __shfl_down_sync(0xffffffffu, pv[0], 1);
+  uint32_t mask = 0u;
+  float bp = 0.0f;  // a local maximum exceeds its left neighbour (>= 0): bp > 0 marks a candidate
+  int bm = -1;
+#pragma unroll
+  for (int m = 0; m < NP; ++m) {
+    const float v = pv[m];
+    const float l = m > 0 ? pv[m > 0 ? m - 1 : 0] : left_in;
+    const float r = m + 1 < NP ? pv[m + 1 < NP ? m + 1 : m] : right_in;
+    const bool loc = m >= lo && m <= hi && v > l && v >= r;
+    if (loc) mask |= 1u << m;
+    if (loc && v > bp) {
+      bp = v;
+      bm = m;
+    }
+  }
+  // the warp's three best
+  unsigned long long wk[3];
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    const uint32_t hb = __float_as_uint(bp);
+    const uint32_t top = __reduce_max_sync(0xffffffffu, hb);
+    const uint32_t ball = __ballot_sync(0xffffffffu, hb == top);
+    const int win = __ffs(ball) - 1;  // the lowest lane: the lowest bin among equal powers
+    const uint32_t kw = __shfl_sync(0xffffffffu, k0 + (uint32_t)bm, win);
+    wk[r] = top ? (((unsigned long long)top << 32) | (unsigned long long)(0xFFFFFFFFu - kw)) : 0ull;
+    if (r < 2 && top && lane == win) {
+      mask &= ~(1u << bm);
+      bp = 0.0f;
+      bm = -1;
+#pragma unroll
+      for (int m = 0; m < NP; ++m)
+        if (((mask >> m) & 1u) && pv[m] > bp) {
+          bp = pv[m];
+          bm = m;
+        }
+    }
+  }
+  // publish: the list, the warp's first two and last two bins, and the
+  // chunk's last two bins where the chunk ends inside a warp
+  if (lane == 0) {
+    red[3 * warp] = wk[0];
+    red[3 * warp + 1] = wk[1];
+    red[3 * warp + 2] = wk[2];
+    pw[4 * warp] = pv[0];
+    if (NP >= 2) pw[4 * warp + 1] = pv[NP >= 2 ? 1 : 0];
+  }
+  if (NP == 1 && lane == 1) pw[4 * warp + 1] = pv[0];
+  if (NP == 1 && lane == 30) pw[4 * warp + 2] = pv[0];
+  if (lane == 31) {
+    if (NP >= 2) pw[4 * warp + 2] = pv[NP >= 2 ? NP - 2 : 0];
+    pw[4 * warp + 3] = pv[NP - 1];
+  }
+  if (nvalid < chunk_len) {
+    const int j0 = nvalid - 1 - base, j1 = nvalid - 2 - base;
+    if ((unsigned)j0 < (unsigned)NP || (unsigned)j1 < (unsigned)NP) {
+#pragma unroll
+      for (int m = 0; m < NP; ++m) {
+        if (m == j0) pw[4 * nw] = pv[m];
+        if (m == j1) pw[4 * nw + 1] = pv[m];
+      }
+    }
+  }
+  __syncthreads();
+  if (warp != 0) return;
+  // lane w < nw: warp w's list with the two bins at its boundary with warp w - 1
+  unsigned long long c0 = 0ull, c1 = 0ull, c2 = 0ull;
+  if (lane < nw) {
+    c0 = red[3 * lane];
+    c1 = red[3 * lane + 1];
+    c2 = red[3 * lane + 2];
+    if (lane > 0) {
+      const int i = lane * 32 * NP;  // chunk index of warp `lane`'s first bin
+      const float f0 = pw[4 * lane], f1 = pw[4 * lane + 1];
+      const float l1 = pw[4 * lane - 2], l0 = pw[4 * lane - 1];
+      unsigned long long e[2] = {0ull, 0ull};
+      if (i - 1 <= nvalid - 2 && l0 > l1 && l0 >= f0) e[0] = pkey(l0, (uint32_t)(k_chunk0 + i - 1));
+      if (i <= nvalid - 2 && f0 > l0 && f0 >= f1) e[1] = pkey(f0, (uint32_t)(k_chunk0 + i));
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        const unsigned long long x = e[q];
+        if (x > c0) {
+          c2 = c1;
+          c1 = c0;
+          c0 = x;
+        } else if (x > c1) {
+          c2 = c1;
+          c1 = x;
+        } else if (x > c2) {
+          c2 = x;
+        }
+      }
+    }
+  }
+  unsigned long long top3[3];
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    const uint32_t h = (uint32_t)(c0 >> 32);
+    const uint32_t th = __reduce_max_sync(0xffffffffu, h);
+    const uint32_t tl = __reduce_max_sync(0xffffffffu, h == th ? (uint32_t)c0 : 0u);
+    const unsigned long long t = ((unsigned long long)th << 32) | tl;
+    top3[r] = t;
+    if (t && c0 == t) {  // keys of distinct bins differ: one lane holds it
+      c0 = c1;
+      c1 = c2;
+      c2 = 0ull;
+    }
+  }
+  if (lane == 0) {
+    const bool full = nvalid == chunk_len;
+    const float first0 = pw[0], first1 = pw[1];
+    const float last0 = full ? pw[4 * nw - 1] : pw[4 * nw];
+    const float last1 = full ? pw[4 * nw - 2] : pw[4 * nw + 1];
+    unsigned long long best = top3[0];
+    if (nvalid > 0) best = umax64(best, pkey(first0, (uint32_t)k_chunk0));
+    if (nvalid > 1) best = umax64(best, pkey(last0, (uint32_t)(k_chunk0 + nvalid - 1)));
+    *best_out = ChunkBest{(double)key_power(best), key_index(best)};
+    ChunkCand out;
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      out.p[r] = (double)key_power(top3[r]);
+      out.k[r] = key_index(top3[r]);
+    }
+    out.k_first = k_chunk0;
+    out.nvalid = nvalid;
+    out.pad = 0;
+    out.first[0] = nvalid > 0 ? (double)first0 : 0.0;
+    out.first[1] = nvalid > 1 ? (double)first1 : 0.0;
+    out.last[0] = nvalid > 0 ? (double)last0 : 0.0;
+    out.last[1] = nvalid > 1 ? (double)last1 : 0.0;
+    *cand_out = out;
+  }
+}
+
+// chunk_results_f32 with the chunk staged in shared memory: the same
+// results (first maximum, top-3 interior local maxima, edge bins), found by
+// a scan of the staged powers and block-wide key reductions.  The
+// generalized periodogram's kernels use it: with the register version their
+// main loop compiled measurably slower (0.745 against 0.792 of the bound on
+// the lognormal batch), more than its cheaper epilogue won back.  `pw` is a
+// shared buffer of blockDim.x * (NP + 1) floats (top-k only).
+template <int NP>
+__device__ void chunk_results_f32_staged(const float (&pv)[NP], uint32_t k0, int64_t k_chunk0, int64_t n_f,
                                   ChunkBest* best_out, ChunkCand* cand_out, float* pw,
                                   unsigned long long* red) {
   unsigned long long best = 0ull;
@@ -640,24 +828,28 @@ __device__ void chunk_results_f32(const float (&pv)[NP], uint32_t k0, int64_t k_
   __syncthreads();
 }
 
-// Eq. 2 from the FP32 single-scan sums with the SFU's reciprocal square root
-// and fast division (relative error ~1e-7, far inside the FP32 path's budget).
-// Also reports whether the bin is ill-conditioned (see kIllConditioned).
+// Eq. 2 from the FP32 single-scan sums, its two terms over one denominator:
+// with W = (2 CC - N) + i 2 CS and Z = XC + i XS as in lsp_power,
+// (N + R)(N - R) = N^2 - |W|^2 and Q R = Re(Z^2 conj W), so
+//   P = (N |Z|^2 - Re(Z^2 conj W)) / (N^2 - |W|^2),
+// one fast division (relative error ~1e-7) and no square root.  Its
+// denominator is N^2 - R^2 = (N + R)(N - R) >= N (N - R), so where the bin
+// is well conditioned (N - R >= 5 % N, ill_conditioned below) it is at
+// least 0.05 N^2; the ill-conditioned bins, R = N included, are re-evaluated
+// in FP64 by the callers.  `ill` is N - R < 5 % N, tested as R^2 > 0.95^2 N^2.
+constexpr float kIllR2 = (1.0f - kIllConditioned) * (1.0f - kIllConditioned);
+
 __device__ __forceinline__ float lsp_power_f32(float xc, float xs, float cc, float cs, float n, bool& ill) {
   const float c2 = fmaf(2.0f, cc, -n);
   const float s2 = 2.0f * cs;
   const float r2 = fmaf(c2, c2, s2 * s2);
-  const float rinv = r2 > 0.0f ? rsqrtf(r2) : 0.0f;
-  const float r = r2 * rinv;
+  const float nn = n * n;
   const float z2 = fmaf(xc, xc, xs * xs);
-  const float q = fmaf((xc - xs) * (xc + xs), c2, 2.0f * xc * xs * s2) * rinv;
-  const float d1 = n + r, d2 = n - r;
-  const float eps = EpsRel<float>::v * n;
-  ill = d2 < kIllConditioned * n;
-  float p = 0.0f;
-  if (0.5f * d1 > eps) p += __fdividef(fmaxf(z2 + q, 0.0f), d1);
-  if (0.5f * d2 > eps) p += __fdividef(fmaxf(z2 - q, 0.0f), d2);
-  return 0.5f * p;
+  const float re = fmaf((xc - xs) * (xc + xs), c2, 2.0f * xc * xs * s2);  // Re(Z^2 conj W)
+  const float num = fmaf(n, z2, -re);
+  const float den = nn - r2;
+  ill = r2 > kIllR2 * nn;
+  return den > 0.0f ? __fdividef(fmaxf(num, 0.0f), den) : 0.0f;
 }
 
 }  // namespace lsp

@@ -25,7 +25,7 @@ int occupancy(Kern kern, int threads, size_t dyn) {
 // abl: ablation code trig + 3 * staging (0: the production kernels); the
 // ablation kernels are scalar, K = 16, standard periodogram only.
 template <typename Fn>
-bool dispatch_f32(int packed, int k, int gls, int abl, Fn&& fn) {
+bool dispatch_f32(int packed, int k, int gls, int abl, int threads, Fn&& fn) {
   if (abl) {
     if (packed || gls || k != 16) return false;
     switch (abl) {
@@ -46,6 +46,18 @@ bool dispatch_f32(int packed, int k, int gls, int abl, Fn&& fn) {
     return false;
   }
   if (packed) {
+    // 64- and 128-thread CTAs of K = 8 and 12: instantiations whose launch
+    // bounds ask for 16 and 12 warps per SM (128 and 168 registers); left
+    // to itself the compiler took 128 to 193 registers for these kernels and
+    // ran 7-13 % slower per pair
+    if (threads == 64 || threads == 128) {
+      switch (k * 1000 + threads) {
+        case 8064: fn(main_f32_packed_floor<8, 64, 8>); return true;
+        case 8128: fn(main_f32_packed_floor<8, 128, 4>); return true;
+        case 12064: fn(main_f32_packed_floor<12, 64, 6>); return true;
+        case 12128: fn(main_f32_packed_floor<12, 128, 3>); return true;
+      }
+    }
     switch (k) {
       case 4: fn(main_f32_packed<4>); return true;
       case 8: fn(main_f32_packed<8>); return true;
@@ -64,13 +76,13 @@ bool dispatch_f32(int packed, int k, int gls, int abl, Fn&& fn) {
 
 bool main_variant_exists_f32(int packed, int k, int fpt, int gls, int abl) {
   if (fpt != (packed ? 2 * k : k)) return false;
-  return dispatch_f32(packed, k, gls, abl, [](auto) {});
+  return dispatch_f32(packed, k, gls, abl, 256, [](auto) {});
 }
 
 int main_blocks_per_sm_f32(int packed, int k, int fpt, int threads, int top, int gls, int abl) {
   int nb = 0;
   size_t dyn = main_dyn_smem(0, fpt, threads, top);
-  dispatch_f32(packed, k, gls, abl, [&](auto kern) { nb = occupancy(kern, threads, dyn); });
+  dispatch_f32(packed, k, gls, abl, threads, [&](auto kern) { nb = occupancy(kern, threads, dyn); });
   return nb;
 }
 
@@ -92,7 +104,7 @@ cudaError_t launch_main_f32(const MainLaunch& ml, cudaStream_t stream) {
   p.win_start = ml.win_start;
   p.win_len = ml.win_len;
   cudaError_t err = cudaErrorInvalidValue;
-  dispatch_f32(ml.packed, ml.k_reseed, ml.gls, ml.abl, [&](auto kern) { err = launch_kernel(kern, ml, p, stream); });
+  dispatch_f32(ml.packed, ml.k_reseed, ml.gls, ml.abl, ml.threads, [&](auto kern) { err = launch_kernel(kern, ml, p, stream); });
   return err;
 }
 

@@ -288,6 +288,20 @@ __device__ __forceinline__ int stage_tile(const uint4* __restrict__ src, int nt,
   return n_cheb;
 }
 
+// Loop over staged observation entries [j0, j1).  kRolled keeps it rolled:
+// the chains of up to 12 frequencies run measurably faster per pair that way
+// (unrolled, their register count rose past the occupancy the launch bounds
+// ask for); the 16-frequency chains gain from the compiler's unrolling.
+template <bool kRolled, typename Fn>
+__device__ __forceinline__ void obs_loop(int j0, int j1, Fn&& fn) {
+  if constexpr (kRolled) {
+#pragma unroll 1
+    for (int j = j0; j < j1; ++j) fn(j);
+  } else {
+    for (int j = j0; j < j1; ++j) fn(j);
+  }
+}
+
 // Seeds of the two packed chains: bins k0 and k0 + K.
 __device__ __forceinline__ void seed_pair_kb(const ObsF2& e, uint32_t k0, f2_t& c2, f2_t& s2) {
   float c0, s0, c1, s1;
@@ -299,7 +313,7 @@ __device__ __forceinline__ void seed_pair_kb(const ObsF2& e, uint32_t k0, f2_t& 
 }
 
 template <int K>
-__global__ void __launch_bounds__(256) main_f32_packed(MainParams<RecF32, float> p) {
+__device__ __forceinline__ void main_f32_packed_body(const MainParams<RecF32, float>& p) {
   constexpr int F = 2 * K;
   __shared__ ObsF2 s_ent[LSP_TILE_OBS];
   __shared__ uint32_t s_bal[LSP_TILE_OBS / 32];
@@ -369,10 +383,10 @@ __global__ void __launch_bounds__(256) main_f32_packed(MainParams<RecF32, float>
       if ((int64_t)k0 < kend) {
         if (n_ch > 0) {
           flip();
-          for (int j = 0; j < n_ch; ++j) obs(s_ent[j], std::true_type{});
+          obs_loop<(K <= 12)>(0, n_ch, [&](int j) { obs(s_ent[j], std::true_type{}); });
           flip();
         }
-        for (int j = n_ch; j < nt; ++j) obs(s_ent[j], std::false_type{});
+        obs_loop<(K <= 12)>(n_ch, nt, [&](int j) { obs(s_ent[j], std::false_type{}); });
       }
       __syncthreads();
     }
@@ -398,7 +412,13 @@ __global__ void __launch_bounds__(256) main_f32_packed(MainParams<RecF32, float>
       fix_ill_conditioned<F>(pv, bad, k0, p.rec, oi.begin, oi.n, oi.norm_scale);
       if (p.power_out) store_row<F>(p.power_out + o * p.n_f, (int64_t)k0, pv, kend);
       const int64_t res = o * (int64_t)n_chunks + chunk;
-      chunk_results_f32<F>(pv, k0, kc0, kend, p.best + res, p.cand ? p.cand + res : nullptr, s_pw, red);
+      // the 16-frequency chains keep the staged epilogue: with the register
+      // one their main loop compiled slower (one large object: 22.9 against
+      // 21.7 ms), more than the epilogue saves
+      if constexpr (K >= 16)
+        chunk_results_f32_staged<F>(pv, k0, kc0, kend, p.best + res, p.cand ? p.cand + res : nullptr, s_pw, red);
+      else
+        chunk_results_f32<F>(pv, k0, kc0, kend, p.best + res, p.cand ? p.cand + res : nullptr, s_pw, red);
     } else {
       float* part = p.part + (int64_t)is * p.n_f * 4;
 #pragma unroll
@@ -413,6 +433,17 @@ __global__ void __launch_bounds__(256) main_f32_packed(MainParams<RecF32, float>
       }
     }
   }
+}
+
+// The standard kernel with the default launch bounds, and with launch bounds
+// that ask for MINB resident CTAs of MAXT threads (a register floor).
+template <int K>
+__global__ void __launch_bounds__(256) main_f32_packed(MainParams<RecF32, float> p) {
+  main_f32_packed_body<K>(p);
+}
+template <int K, int MAXT, int MINB>
+__global__ void __launch_bounds__(MAXT, MINB) main_f32_packed_floor(MainParams<RecF32, float> p) {
+  main_f32_packed_body<K>(p);
 }
 
 // ------------------------------------------------------------------------
@@ -530,7 +561,7 @@ __global__ void __launch_bounds__(256) main_f32_packed_gls(MainParams<RecF32, fl
     fix_ill_conditioned_gls<F>(pv, bad, k0, p.rec, oi);
     if (p.power_out) store_row<F>(p.power_out + o * p.n_f, (int64_t)k0, pv, p.n_f);
     const int64_t res = o * (int64_t)n_chunks + chunk;
-    chunk_results_f32<F>(pv, k0, kc0, p.n_f, p.best + res, p.cand ? p.cand + res : nullptr, s_pw, red);
+    chunk_results_f32_staged<F>(pv, k0, kc0, p.n_f, p.best + res, p.cand ? p.cand + res : nullptr, s_pw, red);
   }
 }
 

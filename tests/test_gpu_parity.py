@@ -208,6 +208,62 @@ def test_fused_argmax_matches_own_power(env, small_batch):
             assert pk["power"][o] == p[o, k]
 
 
+TOP3_VARIANTS = FP32_VARIANTS + [
+    dict(k_reseed=12, freqs_per_thread=24, block_threads=128),
+    dict(k_reseed=8, freqs_per_thread=16, block_threads=64),
+    dict(k_reseed=16, freqs_per_thread=32, block_threads=64),
+    dict(k_reseed=12, freqs_per_thread=24, block_threads=224),
+]
+
+
+def _own_top3(p, pk, n_obj, what):
+    """The fused top-3 against the oracle's local-maximum rule applied to the
+    kernel's own powers (the same FP32 values): bit-exact."""
+    pk = pk.reshape(n_obj, 3)
+    for o in range(n_obj):
+        idx, pw = oracle.top_local_maxima(p[o], 3)
+        np.testing.assert_array_equal(pk["idx"][o], idx, err_msg=f"{what} object {o}")
+        np.testing.assert_array_equal(pk["power"][o], pw, err_msg=f"{what} object {o}")
+
+
+def test_fused_top3_matches_own_power(env):
+    """Top-3 selection (per-thread candidates, warp rounds, the bins at warp
+    and chunk boundaries merged by one warp) against the same rule on the
+    kernel's stored powers: every FP32 variant, a prime grid so the last
+    chunk of each object is ragged, and short objects whose periodograms have
+    a local maximum every bin or two."""
+    b = synth.ragged_lognormal(48, seed=5, grid=synth.Grid(0.24, 12.0, 20011))
+    for var in TOP3_VARIANTS:
+        p, pk = batch(env, b, "fp32", return_power=True, top_k=3, **var)
+        _own_top3(p, pk, b.n_obj, str(var))
+        assert pk["idx"].min() >= 0
+
+
+@pytest.mark.parametrize("split", [3, 16])
+def test_fused_top3_split_single_matches_own_power(env, small_single, split):
+    """The split-N_t combine (one bin per thread) selects the top-3 the same way."""
+    b, _ = small_single
+    p, pk = single(env, b, "fp32", top_k=3, obs_split=split)
+    _own_top3(p[None, :], pk, 1, f"split {split}")
+
+
+def test_fused_top3_gls_matches_own_power(env):
+    """The generalized periodogram's kernels share the FP32 epilogue."""
+    lsp, torch, dev = env
+    b = synth.ragged_lognormal(32, seed=6, grid=synth.Grid(0.24, 12.0, 9001))
+    g = lsp.Grid(b.grid.f_min, b.grid.f_max, b.grid.n_f)
+    t = _dev(torch, dev, b.t, torch.float64)
+    y = _dev(torch, dev, b.y, torch.float32)
+    e = _dev(torch, dev, np.random.default_rng(3).uniform(0.02, 0.3, b.t.size), torch.float32)
+    off = _dev(torch, dev, b.offsets, torch.int64)
+    for var in (dict(k_reseed=8, freqs_per_thread=16, block_threads=64),
+                dict(k_reseed=8, freqs_per_thread=16, block_threads=128),
+                dict(k_reseed=4, freqs_per_thread=8, block_threads=256)):
+        power, peaks = lsp.batch_gls(t, y, e, off, g, return_power=True, top_k=3, **var)
+        torch.cuda.synchronize()
+        _own_top3(power.cpu().numpy().astype(np.float64), lsp.peaks_to_numpy(peaks), b.n_obj, str(var))
+
+
 def test_batch_variants_agree(env, small_batch):
     b, ref = small_batch
     for var in FP32_VARIANTS:
