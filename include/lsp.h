@@ -438,7 +438,11 @@ lsp_status lsp_featurize(const double* t, const float* y, const int64_t* offsets
                          float* feat_f32, lsp_stream_t stream);
 
 /* Logits (batch x n_classes, FP32) of the MLP on bfloat16 inputs x (batch x in_dim);
- * batch <= LSP_MLP_MAX_BATCH rows per call. */
+ * batch <= LSP_MLP_MAX_BATCH rows per call.  The products run on the tcgen05
+ * tensor cores with operands loaded by TMA: when in_dim is a multiple of 8,
+ * x_bf16 must be 16-byte aligned (LSP_E_ARG otherwise; any row of a
+ * contiguous allocation is); other widths are copied to a padded pitch in the
+ * workspace first. */
 #define LSP_MLP_MAX_BATCH 4194240
 lsp_status lsp_mlp_forward(const lsp_mlp_dims* dims, const float* params, const uint16_t* params_bf16,
                            const uint16_t* x_bf16, int64_t batch, float* logits, void* workspace,
@@ -449,7 +453,9 @@ lsp_status lsp_mlp_forward(const lsp_mlp_dims* dims, const float* params, const 
  * into *loss (device float) and its gradient into grad (flat FP32, the
  * parameters' layout).  Hidden activations and back-propagated
  * pre-activation gradients are stored in bfloat16; products accumulate in
- * FP32 on the tensor cores.
+ * FP32 on the tensor cores (the weight gradient's sum over the batch is split
+ * over several CTAs and added in a fixed order, so results are
+ * deterministic).  x_bf16 as for lsp_mlp_forward.
  */
 lsp_status lsp_mlp_loss_grad(const lsp_mlp_dims* dims, const float* params, const uint16_t* params_bf16,
                              const uint16_t* x_bf16, const int32_t* labels, int64_t batch, float* loss,
@@ -460,6 +466,13 @@ lsp_status lsp_mlp_loss_grad(const lsp_mlp_dims* dims, const float* params, cons
 lsp_status lsp_mlp_adamw(int64_t n, float* params, uint16_t* params_bf16, const float* grad, float* m,
                          float* v, int64_t step, float lr, float beta1, float beta2, float eps,
                          float weight_decay, lsp_stream_t stream);
+
+/* Number of tensor-core GEMM tiles of lsp_mlp_forward / lsp_mlp_loss_grad /
+ * lsp_propose_refine on the current device whose bounded device-side waits
+ * (about one second each) gave up since the last call, and reset it to 0.
+ * Such a tile writes NaN over its outputs instead of hanging.  Synchronous
+ * (reads device memory). */
+lsp_status lsp_mlp_gemm_timeouts(uint32_t* count);
 
 /* FP32 -> bfloat16 (round to nearest even). */
 lsp_status lsp_to_bf16(const float* a, uint16_t* b, int64_t n, lsp_stream_t stream);

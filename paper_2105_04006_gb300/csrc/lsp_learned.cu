@@ -10,9 +10,11 @@
 #include <cstdio>
 #include <cstring>
 #include <cuda_bf16.h>
+#include <mutex>
 
 #include "../../include/lsp.h"
 #include "lsp_launch.h"
+#include "lsp_umma.cuh"
 
 namespace lsp {
 void set_last_error(const char* msg);
@@ -195,123 +197,221 @@ __global__ void __launch_bounds__(kFeatThreads) featurize_kernel(
 }
 
 // ===================================================================== GEMM
-// C[M, N] = A[M, K] B[K, N] on the tensor cores (mma.sync m16n8k16, bf16 in,
-// fp32 accumulate).  A and B are read through element strides, so the same
-// kernel serves X W, dZ W^T and A^T dZ.  Epilogue: optional bias (fp32),
-// ReLU, multiplication by the ReLU mask (mask > 0) of a bf16 matrix, and
-// fp32 and/or bf16 outputs (row-major, leading dimension N).
-struct GemmArgs {
+// The network's products run on the tcgen05 tensor cores (lsp_umma.cuh):
+// C[M, N] = A[M, K] B[N, K]^T with both operands K-contiguous bfloat16, read
+// by TMA through tensor maps encoded here.  The forward pass multiplies the
+// activations by the transposed weights (prepared once per call), the input
+// gradient multiplies dZ by the weights, and the weight gradient multiplies
+// the transposed activations by the transposed dZ (both written in that
+// layout by the producing kernels), split over K = batch with a fixed-order
+// reduction of the partial tiles.
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_tiled() {
+  static EncodeTiledFn fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (EncodeTiledFn)p;
+    cudaGetLastError();
+  });
+  return fn;
+}
+
+int64_t ld8(int64_t n) { return (n + 7) / 8 * 8; }  // row pitch (elements) of a TMA-read bfloat16 matrix
+
+// rows x k bfloat16 matrix, K contiguous, pitch ld elements: boxes of
+// box_rows rows x 64 K-elements with the 128-byte swizzle.
+lsp_status make_map(CUtensorMap* map, const bf16* base, int64_t rows, int64_t k, int64_t ld, int box_rows,
+                    const char* what) {
+  EncodeTiledFn enc = encode_tiled();
+  if (!enc) {
+    set_last_error("cuTensorMapEncodeTiled is not available from the driver");
+    return LSP_E_CUDA;
+  }
+  if (((uintptr_t)base) % 16 || (ld * 2) % 16 || ld < k) {
+    char buf[200];
+    snprintf(buf, sizeof buf, "%s: operand not 16-byte aligned or its row pitch not a multiple of 8 elements", what);
+    set_last_error(buf);
+    return LSP_E_ARG;
+  }
+  cuuint64_t dims[2] = {(cuuint64_t)k, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)(ld * 2)};
+  cuuint32_t box[2] = {(cuuint32_t)umma::BK, (cuuint32_t)box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void*)base, dims, strides, box, estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    char buf[200];
+    snprintf(buf, sizeof buf, "%s: cuTensorMapEncodeTiled failed (%d)", what, (int)r);
+    set_last_error(buf);
+    return LSP_E_CUDA;
+  }
+  return LSP_OK;
+}
+
+struct Gemm {
   int M, N, K;
-  const bf16* A;
-  int64_t a_m, a_k;
-  const bf16* B;
-  int64_t b_k, b_n;
+  const bf16* A;  // [M][lda], K contiguous
+  int64_t lda;
+  const bf16* B;  // [N][ldb], K contiguous
+  int64_t ldb;
   const float* bias;
   int relu;
   const bf16* mask;
+  int64_t ldm;
   float* C32;
+  int64_t ldc32;
   bf16* C16;
+  int64_t ldc16;
+  bf16* C16T;
+  int64_t ldt;
+  int splits;     // K split: partial FP32 tiles at part + z M N (pitch N), summed into C32 in order of z
+  float* part;
 };
 
-constexpr int BM = 64, BN = 64, BK = 32, GEMM_THREADS = 128;
+// Split count for a weight-gradient GEMM: about one CTA per SM, at most
+// kMaxSplits partial tiles.
+constexpr int kMaxSplits = 16;
 
-__device__ __forceinline__ uint32_t pack_bf16(bf16 lo, bf16 hi) {
-  return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
+int k_splits(int M, int N, int K) {
+  const int tiles = ((M + umma::BM - 1) / umma::BM) * ((N + umma::MAX_BN - 1) / umma::MAX_BN);
+  const int kb = (K + umma::BK - 1) / umma::BK;
+  int s = 148 / (tiles > 0 ? tiles : 1);
+  s = s < 1 ? 1 : (s > kMaxSplits ? kMaxSplits : s);
+  return s < kb ? s : kb;
 }
 
-__global__ void __launch_bounds__(GEMM_THREADS) gemm_bf16_kernel(GemmArgs g) {
-  __shared__ bf16 As[BM][BK + 8];
-  __shared__ bf16 Bs[BK][BN + 8];
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int gid = lane >> 2, tig = lane & 3;
-  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
-  const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
-  float acc[2][4][4];
-#pragma unroll
-  for (int a = 0; a < 2; ++a)
-#pragma unroll
-    for (int b = 0; b < 4; ++b)
-#pragma unroll
-      for (int c = 0; c < 4; ++c) acc[a][b][c] = 0.0f;
-  const bf16 zero = __float2bfloat16_rn(0.0f);
-  for (int k0 = 0; k0 < g.K; k0 += BK) {
-    for (int idx = tid; idx < BM * BK; idx += GEMM_THREADS) {
-      const int r = idx / BK, c = idx % BK;
-      const int m = m0 + r, k = k0 + c;
-      As[r][c] = (m < g.M && k < g.K) ? g.A[(int64_t)m * g.a_m + (int64_t)k * g.a_k] : zero;
-    }
-    for (int idx = tid; idx < BK * BN; idx += GEMM_THREADS) {
-      const int r = idx / BN, c = idx % BN;
-      const int k = k0 + r, n = n0 + c;
-      Bs[r][c] = (k < g.K && n < g.N) ? g.B[(int64_t)k * g.b_k + (int64_t)n * g.b_n] : zero;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int kk = 0; kk < BK; kk += 16) {
-      uint32_t af[2][4], bfr[4][2];
-#pragma unroll
-      for (int mt = 0; mt < 2; ++mt) {
-        const int r = wm + mt * 16 + gid, c = kk + 2 * tig;
-        af[mt][0] = pack_bf16(As[r][c], As[r][c + 1]);
-        af[mt][1] = pack_bf16(As[r + 8][c], As[r + 8][c + 1]);
-        af[mt][2] = pack_bf16(As[r][c + 8], As[r][c + 9]);
-        af[mt][3] = pack_bf16(As[r + 8][c + 8], As[r + 8][c + 9]);
-      }
-#pragma unroll
-      for (int nt = 0; nt < 4; ++nt) {
-        const int c = wn + nt * 8 + gid, r = kk + 2 * tig;
-        bfr[nt][0] = pack_bf16(Bs[r][c], Bs[r + 1][c]);
-        bfr[nt][1] = pack_bf16(Bs[r + 8][c], Bs[r + 9][c]);
-      }
-#pragma unroll
-      for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-        for (int nt = 0; nt < 4; ++nt) {
-          float* d = acc[mt][nt];
-          asm volatile(
-              "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
-              "{%8,%9}, {%0,%1,%2,%3};"
-              : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-              : "r"(af[mt][0]), "r"(af[mt][1]), "r"(af[mt][2]), "r"(af[mt][3]), "r"(bfr[nt][0]),
-                "r"(bfr[nt][1]));
-        }
-    }
-    __syncthreads();
+__global__ void splitk_reduce_kernel(const float* __restrict__ part, int splits, int64_t mn, int n,
+                                     float* __restrict__ out, int64_t ldo) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < mn; i += (int64_t)gridDim.x * blockDim.x) {
+    float s = 0.0f;
+    for (int z = 0; z < splits; ++z) s += part[z * mn + i];
+    out[(i / n) * ldo + i % n] = s;
   }
-#pragma unroll
-  for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-    for (int nt = 0; nt < 4; ++nt)
-#pragma unroll
-      for (int h = 0; h < 2; ++h)
-#pragma unroll
-        for (int q = 0; q < 2; ++q) {
-          const int m = m0 + wm + mt * 16 + gid + 8 * h;
-          const int n = n0 + wn + nt * 8 + 2 * tig + q;
-          if (m >= g.M || n >= g.N) continue;
-          float v = acc[mt][nt][2 * h + q];
-          if (g.bias) v += g.bias[n];
-          if (g.relu) v = fmaxf(v, 0.0f);
-          const int64_t at = (int64_t)m * g.N + n;
-          if (g.mask && !(__bfloat162float(g.mask[at]) > 0.0f)) v = 0.0f;
-          if (g.C32) g.C32[at] = v;
-          if (g.C16) g.C16[at] = __float2bfloat16_rn(v);
-        }
 }
 
-cudaError_t gemm(const GemmArgs& g, cudaStream_t s) {
-  if (g.M <= 0 || g.N <= 0) return cudaSuccess;
-  dim3 grid((g.N + BN - 1) / BN, (g.M + BM - 1) / BM);
-  gemm_bf16_kernel<<<grid, GEMM_THREADS, 0, s>>>(g);
+// dst[c][r] = src[r][c] for a rows x cols bfloat16 matrix (32 x 32 tiles).
+__global__ void transpose_bf16_kernel(const bf16* __restrict__ src, int64_t rows, int64_t cols, int64_t lds,
+                                      bf16* __restrict__ dst, int64_t ldd) {
+  __shared__ bf16 tile[32][33];
+  const int64_t r0 = (int64_t)blockIdx.x * 32, c0 = (int64_t)blockIdx.y * 32;
+  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+    const int64_t r = r0 + i, c = c0 + threadIdx.x;
+    if (r < rows && c < cols) tile[i][threadIdx.x] = src[r * lds + c];
+  }
+  __syncthreads();
+  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+    const int64_t c = c0 + i, r = r0 + threadIdx.x;
+    if (c < cols && r < rows) dst[c * ldd + r] = tile[threadIdx.x][i];
+  }
+}
+
+// dst[r][c] = src[r][c] with a new row pitch.
+__global__ void repitch_bf16_kernel(const bf16* __restrict__ src, int64_t rows, int64_t cols, int64_t lds,
+                                    bf16* __restrict__ dst, int64_t ldd) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < rows * cols;
+       i += (int64_t)gridDim.x * blockDim.x)
+    dst[(i / cols) * ldd + i % cols] = src[(i / cols) * lds + i % cols];
+}
+
+cudaError_t transpose_bf16(const bf16* src, int64_t rows, int64_t cols, int64_t lds, bf16* dst, int64_t ldd,
+                           cudaStream_t s) {
+  if (rows <= 0 || cols <= 0) return cudaSuccess;
+  dim3 grid((unsigned)((rows + 31) / 32), (unsigned)((cols + 31) / 32));
+  transpose_bf16_kernel<<<grid, dim3(32, 8), 0, s>>>(src, rows, cols, lds, dst, ldd);
   return cudaGetLastError();
+}
+
+cudaError_t repitch_bf16(const bf16* src, int64_t rows, int64_t cols, int64_t lds, bf16* dst, int64_t ldd,
+                         cudaStream_t s) {
+  if (rows <= 0 || cols <= 0) return cudaSuccess;
+  repitch_bf16_kernel<<<1024, 256, 0, s>>>(src, rows, cols, lds, dst, ldd);
+  return cudaGetLastError();
+}
+
+// Shared-memory attributes of the GEMM kernel, once per device: its dynamic
+// size, and the largest carveout so that two CTAs share an SM.
+lsp_status gemm_attributes() {
+  static std::mutex mu;
+  static uint64_t done_mask = 0;
+  int dev = 0;
+  LEARN_CUDA(cudaGetDevice(&dev), "GEMM device");
+  std::lock_guard<std::mutex> lk(mu);
+  if (dev >= 0 && dev < 64 && (done_mask >> dev) & 1u) return LSP_OK;
+  LEARN_CUDA(cudaFuncSetAttribute(umma::gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, umma::SMEM_BYTES),
+             "GEMM shared memory");
+  LEARN_CUDA(cudaFuncSetAttribute(umma::gemm_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                  cudaSharedmemCarveoutMaxShared),
+             "GEMM shared-memory carveout");
+  if (dev >= 0 && dev < 64) done_mask |= (uint64_t)1 << dev;
+  return LSP_OK;
+}
+
+lsp_status gemm(const Gemm& q, cudaStream_t s) {
+  if (q.M <= 0 || q.N <= 0 || q.K <= 0) return LSP_OK;
+  const int n_tile = q.N >= umma::MAX_BN ? umma::MAX_BN : (q.N + 15) / 16 * 16;
+  CUtensorMap ma, mb;
+  lsp_status st = make_map(&ma, q.A, q.M, q.K, q.lda, umma::BM, "GEMM operand A");
+  if (st) return st;
+  if ((st = make_map(&mb, q.B, q.N, q.K, q.ldb, n_tile, "GEMM operand B"))) return st;
+  const int kb = (q.K + umma::BK - 1) / umma::BK;
+  int splits = q.splits < 1 ? 1 : q.splits;
+  const int kb_per = (kb + splits - 1) / splits;
+  splits = (kb + kb_per - 1) / kb_per;  // every split gets at least one K slice
+  umma::Args a;
+  memset(&a, 0, sizeof a);
+  a.M = q.M;
+  a.N = q.N;
+  a.K = q.K;
+  a.n_tile = n_tile;
+  a.kb_per_split = kb_per;
+  a.bias = q.bias;
+  a.relu = q.relu;
+  a.mask = q.mask;
+  a.ldm = q.ldm;
+  a.C16 = q.C16;
+  a.ldc16 = q.ldc16;
+  a.C16T = q.C16T;
+  a.ldt = q.ldt;
+  if (splits > 1) {
+    if (!q.part || q.bias || q.relu || q.mask || q.C16 || q.C16T || !q.C32) {
+      set_last_error("GEMM: a split product takes an FP32 output only");
+      return LSP_E_ARG;
+    }
+    a.C32 = q.part;
+    a.ldc32 = q.N;
+    a.split_stride = (int64_t)q.M * q.N;
+  } else {
+    a.C32 = q.C32;
+    a.ldc32 = q.ldc32;
+  }
+  if ((st = gemm_attributes())) return st;
+  dim3 grid((unsigned)((q.M + umma::BM - 1) / umma::BM), (unsigned)((q.N + n_tile - 1) / n_tile), (unsigned)splits);
+  umma::gemm_kernel<<<grid, umma::THREADS, umma::SMEM_BYTES, s>>>(ma, mb, a);
+  LEARN_CUDA(cudaGetLastError(), "GEMM launch");
+  if (splits > 1) {
+    const int64_t mn = (int64_t)q.M * q.N;
+    splitk_reduce_kernel<<<(unsigned)((mn + 255) / 256 < 1024 ? (mn + 255) / 256 : 1024), 256, 0, s>>>(
+        q.part, splits, mn, q.N, q.C32, q.ldc32);
+    LEARN_CUDA(cudaGetLastError(), "GEMM split reduction");
+  }
+  return LSP_OK;
 }
 
 // ============================================ loss, reductions, optimizer
 // One warp per row: mean softmax cross-entropy terms and dZ = (softmax -
-// onehot) / batch in bf16.
+// onehot) / batch in bf16 (row pitch ldz).
 __global__ void xent_kernel(const float* __restrict__ logits, const int32_t* __restrict__ labels,
                             int64_t batch, int n_cls, float* __restrict__ row_loss,
-                            bf16* __restrict__ dz) {
+                            bf16* __restrict__ dz, int64_t ldz) {
   const int64_t r = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (r >= batch) return;
@@ -327,7 +427,7 @@ __global__ void xent_kernel(const float* __restrict__ logits, const int32_t* __r
   const float inv_b = 1.0f / (float)batch;
   for (int c = lane; c < n_cls; c += 32) {
     const float p = expf(z[c] - m) / s;
-    dz[r * n_cls + c] = __float2bfloat16_rn((p - (c == lab ? 1.0f : 0.0f)) * inv_b);
+    dz[r * ldz + c] = __float2bfloat16_rn((p - (c == lab ? 1.0f : 0.0f)) * inv_b);
   }
   if (lane == 0) row_loss[r] = logf(s) + m - z[lab];
 }
@@ -347,13 +447,18 @@ __global__ void mean_kernel(const float* __restrict__ v, int64_t n, float* out) 
   }
 }
 
-// Column sums of a bf16 [rows x cols] matrix (bias gradients), fixed order.
-__global__ void colsum_kernel(const bf16* __restrict__ m, int64_t rows, int cols, float* __restrict__ out) {
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= cols) return;
+// Row sums of a bf16 [rows x cols] matrix of row pitch ld: the bias
+// gradients from the transposed dZ (features x batch).  One warp per row,
+// lanes along it, a fixed shuffle tree: the same order on every call.
+__global__ void rowsum_kernel(const bf16* __restrict__ m, int rows, int64_t cols, int64_t ld,
+                              float* __restrict__ out) {
+  const int row = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (row >= rows) return;
   float s = 0.0f;
-  for (int64_t r = 0; r < rows; ++r) s += __bfloat162float(m[r * cols + c]);
-  out[c] = s;
+  for (int64_t c = lane; c < cols; c += 32) s += __bfloat162float(m[row * ld + c]);
+  for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+  if (lane == 0) out[row] = s;
 }
 
 __global__ void adamw_kernel(int64_t n, float* __restrict__ p, bf16* __restrict__ p16,
@@ -566,60 +671,119 @@ lsp_status make_layers(const lsp_mlp_dims* d, Layers* L) {
   return LSP_OK;
 }
 
-// MLP scratch: hidden activations (bf16), logits (fp32), two dZ buffers
-// (bf16), per-row losses.
+// MLP scratch.  bfloat16 matrices the GEMMs read through TMA have row
+// pitches rounded up to 8 elements (16 bytes).
+//   wt[l]  (out x in)  transposed weights: forward B operand
+//   act[l] (batch x out) hidden activations; logits (batch x n_cls, FP32)
+//   xin    (batch x in) padded copy of the input when in_dim % 8 != 0
+// training only:
+//   wp[l]  (in x out)  weights at a padded pitch: input-gradient B operand
+//   xT, actT[l] (features x batch) transposed inputs / activations and
+//   dzT[2] (features x batch) transposed dZ: weight-gradient operands
+//   dz[2]  (batch x width) dZ of the current and the previous layer
+//   part   split-K partial weight-gradient tiles; row_loss (batch)
 struct MlpWs {
+  bf16* wt[8];
   bf16* act[8];
   float* logits;
+  bf16* xin;
+  bf16* wp[8];
+  bf16* xT;
+  bf16* actT[8];
   bf16* dz[2];
+  bf16* dzT[2];
+  float* part;
   float* row_loss;
+  int64_t ldb;  // pitch of the transposed (features x batch) matrices
   size_t total;
 };
 
-void mlp_ws_layout(const Layers& L, int64_t batch, char* base, MlpWs* w) {
+void mlp_ws_layout(const Layers& L, int64_t batch, bool training, char* base, MlpWs* w) {
+  memset(w, 0, sizeof *w);
   size_t off = 0;
+  auto take = [&](size_t bytes) {
+    char* at = base ? base + off : nullptr;
+    off = align256(off + bytes);
+    return at;
+  };
   int maxw = 0;
-  for (int l = 0; l < L.n; ++l) maxw = L.out[l] > maxw ? L.out[l] : maxw;
-  for (int l = 0; l + 1 < L.n; ++l) {
-    w->act[l] = (bf16*)(base + off);
-    off = align256(off + (size_t)batch * L.out[l] * sizeof(bf16));
+  int64_t max_mn = 0;
+  for (int l = 0; l < L.n; ++l) {
+    maxw = L.out[l] > maxw ? L.out[l] : maxw;
+    max_mn = (int64_t)L.in[l] * L.out[l] > max_mn ? (int64_t)L.in[l] * L.out[l] : max_mn;
   }
-  w->logits = (float*)(base + off);
-  off = align256(off + (size_t)batch * L.out[L.n - 1] * sizeof(float));
-  for (int i = 0; i < 2; ++i) {
-    w->dz[i] = (bf16*)(base + off);
-    off = align256(off + (size_t)batch * maxw * sizeof(bf16));
+  w->ldb = ld8(batch);
+  for (int l = 0; l < L.n; ++l) w->wt[l] = (bf16*)take((size_t)L.out[l] * ld8(L.in[l]) * sizeof(bf16));
+  for (int l = 0; l + 1 < L.n; ++l) w->act[l] = (bf16*)take((size_t)batch * ld8(L.out[l]) * sizeof(bf16));
+  w->logits = (float*)take((size_t)batch * L.out[L.n - 1] * sizeof(float));
+  if (L.in[0] % 8) w->xin = (bf16*)take((size_t)batch * ld8(L.in[0]) * sizeof(bf16));
+  if (training) {
+    for (int l = 1; l < L.n; ++l) w->wp[l] = (bf16*)take((size_t)L.in[l] * ld8(L.out[l]) * sizeof(bf16));
+    w->xT = (bf16*)take((size_t)L.in[0] * w->ldb * sizeof(bf16));
+    for (int l = 0; l + 1 < L.n; ++l) w->actT[l] = (bf16*)take((size_t)L.out[l] * w->ldb * sizeof(bf16));
+    for (int i = 0; i < 2; ++i) {
+      w->dz[i] = (bf16*)take((size_t)batch * ld8(maxw) * sizeof(bf16));
+      w->dzT[i] = (bf16*)take((size_t)maxw * w->ldb * sizeof(bf16));
+    }
+    w->part = (float*)take((size_t)kMaxSplits * max_mn * sizeof(float));
+    w->row_loss = (float*)take((size_t)batch * sizeof(float));
   }
-  w->row_loss = (float*)(base + off);
-  off = align256(off + (size_t)batch * sizeof(float));
   w->total = off;
 }
 
-lsp_status mlp_forward_impl(const Layers& L, const float* p32, const bf16* p16, const bf16* x,
-                            int64_t batch, const MlpWs& w, cudaStream_t s) {
+// Transposed weights of every layer (the forward GEMMs' B operands).
+lsp_status prep_forward_weights(const Layers& L, const bf16* p16, const MlpWs& w, cudaStream_t s) {
+  for (int l = 0; l < L.n; ++l)
+    LEARN_CUDA(transpose_bf16(p16 + L.w_off[l], L.in[l], L.out[l], L.out[l], w.wt[l], ld8(L.in[l]), s),
+               "MLP weight transpose");
+  return LSP_OK;
+}
+
+// Logits of `batch` rows of x (row pitch in_dim).  With `training`, every
+// layer's output is also written transposed (the weight-gradient operands).
+lsp_status mlp_forward_impl(const Layers& L, const float* p32, const bf16* x, int64_t batch, const MlpWs& w,
+                            bool training, cudaStream_t s) {
   const bf16* a = x;
+  int64_t lda = L.in[0];
+  if (w.xin) {
+    LEARN_CUDA(repitch_bf16(x, batch, L.in[0], L.in[0], w.xin, ld8(L.in[0]), s), "MLP input copy");
+    a = w.xin;
+    lda = ld8(L.in[0]);
+  }
   for (int l = 0; l < L.n; ++l) {
-    GemmArgs g;
+    Gemm g;
     memset(&g, 0, sizeof g);
     g.M = (int)batch;
     g.N = L.out[l];
     g.K = L.in[l];
     g.A = a;
-    g.a_m = L.in[l];
-    g.a_k = 1;
-    g.B = p16 + L.w_off[l];
-    g.b_k = L.out[l];
-    g.b_n = 1;
+    g.lda = lda;
+    g.B = w.wt[l];
+    g.ldb = ld8(L.in[l]);
     g.bias = p32 + L.b_off[l];
+    g.splits = 1;
     if (l + 1 < L.n) {
       g.relu = 1;
       g.C16 = w.act[l];
+      g.ldc16 = ld8(L.out[l]);
+      if (training) {
+        g.C16T = w.actT[l];
+        g.ldt = w.ldb;
+      }
       a = w.act[l];
+      lda = ld8(L.out[l]);
     } else {
       g.C32 = w.logits;
+      g.ldc32 = L.out[l];
     }
-    LEARN_CUDA(gemm(g, s), "MLP forward GEMM");
+    lsp_status st = gemm(g, s);
+    if (st) return st;
   }
+  return LSP_OK;
+}
+
+lsp_status check_x(const uint16_t* x, int in_dim) {
+  if (in_dim % 8 == 0 && ((uintptr_t)x) % 16) return err_arg("x_bf16 must be 16-byte aligned");
   return LSP_OK;
 }
 
@@ -643,11 +807,10 @@ lsp_status lsp_mlp_workspace_size(const lsp_mlp_dims* dims, int64_t batch, size_
   lsp_status st = make_layers(dims, &L);
   if (st) return st;
   MlpWs w;
-  mlp_ws_layout(L, batch, nullptr, &w);
+  mlp_ws_layout(L, batch, true, nullptr, &w);
   *bytes = w.total;
   return LSP_OK;
 }
-
 lsp_status lsp_featurize(const double* t, const float* y, const int64_t* offsets, int64_t n_obj,
                          int64_t total_nt, const lsp_grid* grid, float lag_max, uint16_t* feat_bf16,
                          float* feat_f32, lsp_stream_t stream) {
@@ -670,12 +833,14 @@ lsp_status lsp_mlp_forward(const lsp_mlp_dims* dims, const float* params, const 
   if (st) return st;
   if (batch < 1 || !params || !params_bf16 || !x_bf16 || !logits) return err_arg("NULL argument");
   if (batch > LSP_MLP_MAX_BATCH) return err_arg("batch exceeds LSP_MLP_MAX_BATCH rows");
+  if ((st = check_x(x_bf16, L.in[0]))) return st;
   MlpWs w;
-  mlp_ws_layout(L, batch, (char*)workspace, &w);
+  mlp_ws_layout(L, batch, false, (char*)workspace, &w);
   if (!workspace || ws_bytes < w.total) return err_arg("MLP workspace too small");
   w.logits = logits;
-  return mlp_forward_impl(L, params, (const bf16*)params_bf16, (const bf16*)x_bf16, batch, w,
-                          (cudaStream_t)stream);
+  cudaStream_t s = (cudaStream_t)stream;
+  if ((st = prep_forward_weights(L, (const bf16*)params_bf16, w, s))) return st;
+  return mlp_forward_impl(L, params, (const bf16*)x_bf16, batch, w, false, s);
 }
 
 lsp_status lsp_mlp_loss_grad(const lsp_mlp_dims* dims, const float* params, const uint16_t* params_bf16,
@@ -687,57 +852,77 @@ lsp_status lsp_mlp_loss_grad(const lsp_mlp_dims* dims, const float* params, cons
   if (batch < 1 || !params || !params_bf16 || !x_bf16 || !labels || !loss || !grad)
     return err_arg("NULL argument");
   if (batch > LSP_MLP_MAX_BATCH) return err_arg("batch exceeds LSP_MLP_MAX_BATCH rows");
+  if ((st = check_x(x_bf16, L.in[0]))) return st;
   MlpWs w;
-  mlp_ws_layout(L, batch, (char*)workspace, &w);
+  mlp_ws_layout(L, batch, true, (char*)workspace, &w);
   if (!workspace || ws_bytes < w.total) return err_arg("MLP workspace too small");
   cudaStream_t s = (cudaStream_t)stream;
   const bf16* p16 = (const bf16*)params_bf16;
   const bf16* x = (const bf16*)x_bf16;
-  if ((st = mlp_forward_impl(L, params, p16, x, batch, w, s))) return st;
+  if ((st = prep_forward_weights(L, p16, w, s))) return st;
+  for (int l = 1; l < L.n; ++l)
+    LEARN_CUDA(repitch_bf16(p16 + L.w_off[l], L.in[l], L.out[l], L.out[l], w.wp[l], ld8(L.out[l]), s),
+               "MLP weight copy");
+  LEARN_CUDA(transpose_bf16(x, batch, L.in[0], L.in[0], w.xT, w.ldb, s), "MLP input transpose");
+  if ((st = mlp_forward_impl(L, params, x, batch, w, true, s))) return st;
   const int n_cls = L.out[L.n - 1];
   const int64_t warps_per_cta = 8;
   xent_kernel<<<(unsigned)((batch + warps_per_cta - 1) / warps_per_cta), 256, 0, s>>>(
-      w.logits, labels, batch, n_cls, w.row_loss, w.dz[0]);
+      w.logits, labels, batch, n_cls, w.row_loss, w.dz[0], ld8(n_cls));
   mean_kernel<<<1, 1024, 0, s>>>(w.row_loss, batch, loss);
   LEARN_CUDA(cudaGetLastError(), "loss");
+  LEARN_CUDA(transpose_bf16(w.dz[0], batch, n_cls, ld8(n_cls), w.dzT[0], w.ldb, s), "dZ transpose");
   int cur = 0;
   for (int l = L.n - 1; l >= 0; --l) {
-    const bf16* a_in = l == 0 ? x : w.act[l - 1];
-    // dW_l = A_in^T dZ_l  (in x out)
-    GemmArgs g;
+    // dW_l = A_in^T dZ_l  (in x out): both operands transposed, K = batch
+    Gemm g;
     memset(&g, 0, sizeof g);
     g.M = L.in[l];
     g.N = L.out[l];
     g.K = (int)batch;
-    g.A = a_in;
-    g.a_m = 1;
-    g.a_k = L.in[l];
-    g.B = w.dz[cur];
-    g.b_k = L.out[l];
-    g.b_n = 1;
+    g.A = l == 0 ? w.xT : w.actT[l - 1];
+    g.lda = w.ldb;
+    g.B = w.dzT[cur];
+    g.ldb = w.ldb;
     g.C32 = grad + L.w_off[l];
-    LEARN_CUDA(gemm(g, s), "MLP weight gradient");
-    colsum_kernel<<<(L.out[l] + 255) / 256, 256, 0, s>>>(w.dz[cur], batch, L.out[l], grad + L.b_off[l]);
+    g.ldc32 = L.out[l];
+    g.splits = k_splits(g.M, g.N, g.K);
+    g.part = w.part;
+    if ((st = gemm(g, s))) return st;
+    rowsum_kernel<<<(L.out[l] + 7) / 8, 256, 0, s>>>(w.dzT[cur], L.out[l], batch, w.ldb, grad + L.b_off[l]);
+    LEARN_CUDA(cudaGetLastError(), "bias gradient");
     if (l > 0) {
-      // dZ_{l-1} = (dZ_l W_l^T) * (A_{l-1} > 0)
-      GemmArgs h;
+      // dZ_{l-1} = (dZ_l W_l^T) * (A_{l-1} > 0), also written transposed
+      Gemm h;
       memset(&h, 0, sizeof h);
       h.M = (int)batch;
       h.N = L.in[l];
       h.K = L.out[l];
       h.A = w.dz[cur];
-      h.a_m = L.out[l];
-      h.a_k = 1;
-      h.B = p16 + L.w_off[l];
-      h.b_k = 1;
-      h.b_n = L.out[l];
+      h.lda = ld8(L.out[l]);
+      h.B = w.wp[l];
+      h.ldb = ld8(L.out[l]);
       h.mask = w.act[l - 1];
+      h.ldm = ld8(L.in[l]);
       h.C16 = w.dz[1 - cur];
-      LEARN_CUDA(gemm(h, s), "MLP input gradient");
+      h.ldc16 = ld8(L.in[l]);
+      h.C16T = w.dzT[1 - cur];
+      h.ldt = w.ldb;
+      h.splits = 1;
+      if ((st = gemm(h, s))) return st;
       cur = 1 - cur;
     }
   }
-  LEARN_CUDA(cudaGetLastError(), "MLP backward");
+  return LSP_OK;
+}
+
+lsp_status lsp_mlp_gemm_timeouts(uint32_t* count) {
+  if (!count) return err_arg("count is NULL");
+  unsigned int v = 0;
+  LEARN_CUDA(cudaMemcpyFromSymbol(&v, umma::g_umma_timeouts, sizeof v), "reading the GEMM wait counter");
+  const unsigned int zero = 0;
+  LEARN_CUDA(cudaMemcpyToSymbol(umma::g_umma_timeouts, &zero, sizeof zero), "clearing the GEMM wait counter");
+  *count = v;
   return LSP_OK;
 }
 
@@ -947,7 +1132,7 @@ namespace {
 constexpr int64_t kProposeRows = (int64_t)1 << 20;
 
 struct ProposeLayout {
-  size_t off_feat, off_act[2], off_logits, off_cls, off_refine, total;
+  size_t off_feat, off_wt[8], off_act[2], off_logits, off_cls, off_refine, total;
   RefineLayout r;
 };
 
@@ -963,7 +1148,8 @@ void propose_layout(const Layers& L, int64_t n_obj, int64_t total_nt, int64_t n_
   int maxw = 0;
   for (int l = 0; l + 1 < L.n; ++l) maxw = L.out[l] > maxw ? L.out[l] : maxw;
   const int64_t rows = n_obj < kProposeRows ? n_obj : kProposeRows;
-  for (int i = 0; i < 2; ++i) p->off_act[i] = take((size_t)rows * maxw * sizeof(bf16));
+  for (int l = 0; l < L.n; ++l) p->off_wt[l] = take((size_t)L.out[l] * ld8(L.in[l]) * sizeof(bf16));
+  for (int i = 0; i < 2; ++i) p->off_act[i] = take((size_t)rows * ld8(maxw) * sizeof(bf16));
   p->off_logits = take((size_t)rows * L.out[L.n - 1] * sizeof(float));
   p->off_cls = take((size_t)n_obj * k_windows * sizeof(int32_t));
   refine_layout(n_obj, total_nt, n_f, &p->r);
@@ -1039,13 +1225,13 @@ lsp_status lsp_propose_refine(const lsp_proposer* net, const double* t, const fl
   // 3. the k best window classes per object, a pass of rows at a time
   MlpWs w;
   memset(&w, 0, sizeof w);
+  for (int l = 0; l < L.n; ++l) w.wt[l] = (bf16*)(ws + p.off_wt[l]);
   for (int l = 0; l + 1 < L.n; ++l) w.act[l] = (bf16*)(ws + p.off_act[l & 1]);
   w.logits = (float*)(ws + p.off_logits);
+  if ((st = prep_forward_weights(L, (const bf16*)net->params_bf16, w, s))) return st;
   for (int64_t r0 = 0; r0 < n_obj; r0 += kProposeRows) {
     const int64_t rows = n_obj - r0 < kProposeRows ? n_obj - r0 : kProposeRows;
-    if ((st = mlp_forward_impl(L, net->params, (const bf16*)net->params_bf16, feat + r0 * LSP_FEAT_DIM, rows, w,
-                               s)))
-      return st;
+    if ((st = mlp_forward_impl(L, net->params, feat + r0 * LSP_FEAT_DIM, rows, w, false, s))) return st;
     topk_kernel<<<(unsigned)((rows + 127) / 128), 128, 0, s>>>(w.logits, rows, L.out[L.n - 1], net->k_windows,
                                                                 cls + r0 * net->k_windows);
     LEARN_CUDA(cudaGetLastError(), "top classes");

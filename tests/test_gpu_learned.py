@@ -341,7 +341,7 @@ def test_propose_refine_one_call_equals_four_calls(env, labelled):
     torch.cuda.synchronize()
     assert torch.equal(cls_one, cls)
     assert torch.equal(pk1, pk2) and torch.equal(info1, info2)
-    assert len(set(cls[:, 0].cpu().tolist())) > 5
+    assert len(set(map(tuple, cls.cpu().tolist()))) > 5  # the proposal lists differ between objects
 
 
 def test_window_labels_follow_the_rule(env, labelled):
