@@ -620,6 +620,15 @@ def learned_leg(args, dev, gpu_index, log=None):
     ms_learned = timed(learned)
     clk.mark(1)
     clocks = clk.stop()
+    # the same path as its parts, each timed alone: features, MLP + top-k
+    # (the tcgen05 GEMMs), windowed refine + full-grid fallback
+    x16 = L.featurize(t, y, off, g)
+    cls = prop.propose(x16)
+    stages = {"featurize_ms": timed(lambda: L.featurize(t, y, off, g)),
+              "mlp_topk_ms": timed(lambda: prop.propose(x16)),
+              "refine_fallback_ms": timed(lambda: L.refine(t, y, off, g, cls, prop.k_windows, prop.stop_power,
+                                                           prop.fallback_power, prop.inconclusive_fallback))}
+    del x16, cls
     full = lsp.peaks_to_numpy(peaks_plain)
     got = lsp.peaks_to_numpy(out["peaks"])
     info = out["info"].cpu().numpy()
@@ -640,8 +649,79 @@ def learned_leg(args, dev, gpu_index, log=None):
             "fallback_fraction": float(fb.mean()), "mean_windows": float(rounds.mean()),
             "pair_fraction": pairs / float(b.pairs), "stop_power": prop.stop_power,
             "trained_on": trained_on, "entry_point": "lsp_propose_refine (one call per step)",
+            "stages": stages,
             "steps": args.steps, "warmup": args.warmup, "l2": "flushed between steps (256 MiB write)",
             "clocks": clocks}
+
+
+def run_mlp(args):
+    """The proposal network's products on the tcgen05 tensor cores: forward
+    passes of the survey network (512 -> 256 -> 256 -> 256 -> 98) on 20 000
+    and 100 000 rows and loss + gradient at batches of 1024 and 4096, device
+    time per call (CUDA events, L2 flushed), against the measured bf16 tensor
+    peak and the HBM bytes the pass moves."""
+    import torch
+    from paper_2105_04006_gb300 import learned as L
+
+    rank, world, local = dist_env()
+    if world > 1:
+        raise SystemExit("--mlp runs on one GPU")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    prop = L.Proposer(100_000, dev, seed=1)
+    d = prop.dims
+    macs = sum(a * b for a, b in [(d.in_dim, d.hidden)] + [(d.hidden, d.hidden)] * (d.n_hidden - 1)
+               + [(d.hidden, d.n_classes)])
+    macs_dx = macs - d.in_dim * d.hidden  # no input gradient for the first layer
+    peaks = {}
+    if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")):
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    tflops_peak, hbm_peak = peaks.get("bf16_tflops"), peaks.get("hbm_gbs")
+    gen = torch.Generator(device="cpu").manual_seed(7)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def timed(fn):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        ms = []
+        for i in range(args.steps):
+            flush.fill_(i & 0xFF)
+            a, c = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            fn()
+            c.record()
+            c.synchronize()
+            ms.append(a.elapsed_time(c))
+        return statistics.mean(ms)
+
+    legs = []
+    for rows in (20_000, 100_000):
+        x16 = torch.randn(rows, d.in_dim, generator=gen).to(torch.bfloat16).to(dev)
+        ms = timed(lambda: prop.forward(x16))
+        flops = 2.0 * rows * macs
+        hbm = rows * (2 * d.in_dim + 2 * 2 * d.hidden * d.n_hidden + 4 * d.n_classes)
+        legs.append({"pass": "forward", "rows": rows, "ms": ms, "tflops": flops / ms / 1e9,
+                     "frac_bf16_peak": flops / ms / 1e9 / tflops_peak if tflops_peak else None,
+                     "hbm_bytes": hbm, "gbs": hbm / ms / 1e6,
+                     "frac_hbm_peak": hbm / ms / 1e6 / hbm_peak if hbm_peak else None})
+    for batch in (1024, 4096):
+        x16 = torch.randn(batch, d.in_dim, generator=gen).to(torch.bfloat16).to(dev)
+        lab = torch.randint(0, d.n_classes, (batch,), generator=gen, dtype=torch.int32).to(dev)
+        ms = timed(lambda: prop.loss_grad(x16, lab))
+        flops = 2.0 * batch * (2 * macs + macs_dx)
+        legs.append({"pass": "loss_grad", "rows": batch, "ms": ms, "tflops": flops / ms / 1e9,
+                     "frac_bf16_peak": flops / ms / 1e9 / tflops_peak if tflops_peak else None})
+    line = {"impl": "gb300", "metric": "proposal-network GEMMs (tcgen05 + TMA): device ms per call",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "dtype": "bf16 x bf16 -> f32",
+            "data": "synthetic", "config": {"workload": "mlp", "network": f"{d.in_dim}-{d.hidden}x{d.n_hidden}-"
+                                                                        f"{d.n_classes}",
+                                            "l2": "flushed between steps (256 MiB write)",
+                                            "hbm_bytes": "forward: inputs read, hidden activations written "
+                                                         "and read back, FP32 logits written"},
+            "legs": legs, "peaks": {"bf16_tflops": tflops_peak, "hbm_gbs": hbm_peak}}
+    print(json.dumps(line), flush=True)
+    return 0
 
 
 OTHER_LEGS = (("ragged_survey", "fp32"), ("single_small", "fp32"), ("single_small", "fp64"),
@@ -1005,6 +1085,8 @@ def main():
                          "[,trig,staging]")
     ap.add_argument("--periodogram-return", action="store_true",
                     help="time the routes that return a full periodogram to the host (Section 3.5)")
+    ap.add_argument("--mlp", action="store_true",
+                    help="time the proposal network's tensor-core GEMMs (forward and loss + gradient)")
     ap.add_argument("--gls", action="store_true",
                     help="the generalized periodogram (photometric errors, floating mean) on a batch workload")
     ap.add_argument("--ablations", action="store_true",
@@ -1017,6 +1099,11 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
+    if args.mlp:
+        if args.impl == "reference":
+            print(json.dumps({"impl": "reference", "unavailable": "the proposal network has no CPU reference arm"}))
+            return 0
+        return run_mlp(args)
     if args.workload == "learned":
         if args.impl == "reference":
             print(json.dumps({"impl": "reference", "unavailable": "the learned stage has no CPU reference arm"}))
