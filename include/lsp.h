@@ -474,6 +474,16 @@ lsp_status lsp_mlp_adamw(int64_t n, float* params, uint16_t* params_bf16, const 
  * (reads device memory). */
 lsp_status lsp_mlp_gemm_timeouts(uint32_t* count);
 
+/* Self-test of those bounded waits: one GEMM tile whose first operand slice
+ * is deliberately never loaded, so the tile's wait for it runs out after
+ * about one second.  Synchronizes the stream, then reports the timeout count
+ * of that launch (1 expected) and how many of its 128 x 16 outputs are NaN
+ * (2048 expected); the device stays usable.  workspace: device memory of at
+ * least LSP_MLP_WAIT_TEST_BYTES, 256-byte aligned, overwritten. */
+#define LSP_MLP_WAIT_TEST_BYTES 65536
+lsp_status lsp_mlp_gemm_wait_test(void* workspace, size_t ws_bytes, uint32_t* timeouts, int32_t* nan_outputs,
+                                  lsp_stream_t stream);
+
 /* FP32 -> bfloat16 (round to nearest even). */
 lsp_status lsp_to_bf16(const float* a, uint16_t* b, int64_t n, lsp_stream_t stream);
 

@@ -94,6 +94,7 @@ EXPORTS = [
     "lsp_probe_fma_rates", "lsp_plan_autotune_ex", "lsp_plan_set_host_parts", "lsp_plan_get_host_parts",
     "lsp_propose_refine", "lsp_propose_refine_workspace_size", "lsp_window_labels", "lsp_noalloc_prepare",
     "lsp_plan_gate_report", "lsp_probe_sincos_fixed64", "lsp_mlp_gemm_timeouts",
+    "lsp_mlp_gemm_wait_test",
 ]
 
 
@@ -158,6 +159,7 @@ def lib():
             L.lsp_mlp_adamw.argtypes = [i64, P, P, P, P, P, i64, f32, f32, f32, f32, f32, P]
             L.lsp_to_bf16.argtypes = [P, P, i64, P]
             L.lsp_mlp_gemm_timeouts.argtypes = [ctypes.POINTER(ctypes.c_uint32)]
+            L.lsp_mlp_gemm_wait_test.argtypes = [P, sz, ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(i32), P]
             L.lsp_top_classes.argtypes = [P, i64, i32, i32, P, P]
             L.lsp_refine_workspace_size.argtypes = [i64, i64, GP, ctypes.POINTER(sz)]
             L.lsp_refine_windows.argtypes = [P, P, P, i64, i64, GP, i32, P, i32, i64, i64, f32, f32, i32, P,

@@ -916,6 +916,46 @@ lsp_status lsp_mlp_loss_grad(const lsp_mlp_dims* dims, const float* params, cons
   return LSP_OK;
 }
 
+lsp_status lsp_mlp_gemm_wait_test(void* workspace, size_t ws_bytes, uint32_t* timeouts, int32_t* nan_outputs,
+                                  lsp_stream_t stream) {
+  if (!workspace || ws_bytes < LSP_MLP_WAIT_TEST_BYTES || ((uintptr_t)workspace) % 256 || !timeouts ||
+      !nan_outputs)
+    return err_arg("wait test: NULL argument or workspace smaller than LSP_MLP_WAIT_TEST_BYTES");
+  cudaStream_t s = (cudaStream_t)stream;
+  // one 128 x 16 tile over one K slice of 64: A 16 KiB, B 2 KiB, C 8 KiB
+  char* ws = (char*)workspace;
+  bf16* A = (bf16*)ws;
+  bf16* B = (bf16*)(ws + 16384);
+  float* C = (float*)(ws + 16384 + 2048);
+  LEARN_CUDA(cudaMemsetAsync(ws, 0, 16384 + 2048, s), "wait test inputs");
+  uint32_t before = 0;
+  lsp_status st = lsp_mlp_gemm_timeouts(&before);  // clears the count
+  if (st) return st;
+  CUtensorMap ma, mb;
+  if ((st = make_map(&ma, A, 128, 64, 64, umma::BM, "wait test A"))) return st;
+  if ((st = make_map(&mb, B, 16, 64, 64, 16, "wait test B"))) return st;
+  if ((st = gemm_attributes())) return st;
+  umma::Args a;
+  memset(&a, 0, sizeof a);
+  a.M = 128;
+  a.N = 16;
+  a.K = 64;
+  a.n_tile = 16;
+  a.kb_per_split = 1;
+  a.C32 = C;
+  a.ldc32 = 16;
+  a.withhold_first_load = 1;
+  umma::gemm_kernel<<<1, umma::THREADS, umma::SMEM_BYTES, s>>>(ma, mb, a);
+  LEARN_CUDA(cudaGetLastError(), "wait test launch");
+  LEARN_CUDA(cudaStreamSynchronize(s), "wait test");
+  float host[128 * 16];
+  LEARN_CUDA(cudaMemcpy(host, C, sizeof host, cudaMemcpyDeviceToHost), "wait test result");
+  int32_t nans = 0;
+  for (int i = 0; i < 128 * 16; ++i) nans += host[i] != host[i];
+  *nan_outputs = nans;
+  return lsp_mlp_gemm_timeouts(timeouts);
+}
+
 lsp_status lsp_mlp_gemm_timeouts(uint32_t* count) {
   if (!count) return err_arg("count is NULL");
   unsigned int v = 0;

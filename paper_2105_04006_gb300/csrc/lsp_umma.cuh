@@ -62,6 +62,7 @@ struct Args {
   int64_t ldc16;
   bf16* C16T;        // [N][ldt] (transposed) or NULL
   int64_t ldt;
+  int withhold_first_load;  // wait test only: the first K slice is never loaded, so its waits run out
 };
 
 __device__ unsigned int g_umma_timeouts;
@@ -225,16 +226,18 @@ __global__ void __launch_bounds__(THREADS, 2)
         break;
       }
       mbar_expect_tx(full0 + 8 * s, stage_bytes);
-      tma_load_2d(a_ring + s * A_STAGE, &map_a, (kb0 + i) * BK, m0, full0 + 8 * s);
-      tma_load_2d(b_ring + s * B_STAGE, &map_b, (kb0 + i) * BK, n0, full0 + 8 * s);
+      if (!(i == 0 && g.withhold_first_load)) {
+        tma_load_2d(a_ring + s * A_STAGE, &map_a, (kb0 + i) * BK, m0, full0 + 8 * s);
+        tma_load_2d(b_ring + s * B_STAGE, &map_b, (kb0 + i) * BK, n0, full0 + 8 * s);
+      }
       issued = i + 1;
     }
-    // no copy may still be landing when the CTA exits
-    for (int i = issued > STAGES ? issued - STAGES : 0; i < issued; ++i)
-      if (!mbar_wait(full0 + 8 * (i % STAGES), (uint32_t)(i / STAGES) & 1u, nullptr)) {
-        *abort_flag = 1;
-        break;
-      }
+    // no copy may still be landing when the CTA exits: wait (bounded) for
+    // every stage's last load
+    for (int i = issued > STAGES ? issued - STAGES : 0; i < issued; ++i) {
+      if (i == 0 && g.withhold_first_load) continue;  // nothing in flight
+      if (!mbar_wait(full0 + 8 * (i % STAGES), (uint32_t)(i / STAGES) & 1u, nullptr)) *abort_flag = 1;
+    }
   } else if (warp == 1 && lane == 0) {
     // ---- MMA issuer
     const uint32_t idesc = idesc_bf16_f32(g.n_tile);

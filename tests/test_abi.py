@@ -191,6 +191,12 @@ def test_newer_entry_points_validate_without_launch(lsp_mod):
     assert L.lsp_propose_refine(ctypes.byref(bad_net), *args, P(4096), 1 << 30, None) == 1
     assert b"LSP_FEAT_DIM" in L.lsp_last_error()
     assert L.lsp_window_labels(P(256), 3, 0, 98, P(512), None) == 1  # stride must be >= 1
+    # tensor-core MLP: a misaligned input is refused before any launch, as is a short wait-test workspace
+    x_bad = P(256 + 2)
+    assert L.lsp_mlp_forward(ctypes.byref(dims), P(256), P(512), x_bad, 4, P(1024), P(4096), 1 << 30, None) == 1
+    assert b"16-byte aligned" in L.lsp_last_error()
+    t_out, n_out = ctypes.c_uint32(), ctypes.c_int32()
+    assert L.lsp_mlp_gemm_wait_test(P(256), 1024, ctypes.byref(t_out), ctypes.byref(n_out), None) == 1
     # grid rule
     assert lsp_mod.grid_for_span(0.24, 12.0, 3650.0).n_f == round((12.0 - 0.24) / (0.1 / 3650.0))
 

@@ -109,3 +109,21 @@ def test_gemm_shapes_against_oracle(env, in_dim, hidden, n_hidden, n_cls, batch)
             worst.append((name, float(r[i]), float(gref[at + i]), float(grad[at + i])))
             at += n
     assert all(w[1] <= 1.0 for w in worst), worst
+
+
+def test_gemm_wait_runs_out_and_the_device_stays_usable(env):
+    """A tile whose first operand slice is withheld: its wait gives up after
+    about a second, the kernel returns on its own, its outputs are NaN and the
+    timeout is counted; the next network call is exact again."""
+    lsp, torch, dev = env
+    L = lsp.lib()
+    ws = torch.empty(65536, dtype=torch.uint8, device=dev)
+    timeouts, nans = ctypes.c_uint32(0), ctypes.c_int32(0)
+    s = ctypes.c_void_p(torch.cuda.current_stream(dev).cuda_stream)
+    st = L.lsp_mlp_gemm_wait_test(ctypes.c_void_p(ws.data_ptr()), ws.numel(), ctypes.byref(timeouts),
+                                  ctypes.byref(nans), s)
+    assert st == 0, L.lsp_last_error()
+    assert timeouts.value == 1 and nans.value == 128 * 16
+    shapes, theta, xv, labv, out = _run(env, 36, 40, 2, 7, 77, seed=113)
+    _, _, inter = OL.loss_and_grad(theta, xv, labv, shapes, bf16_mode=True, return_intermediates=True)
+    np.testing.assert_array_equal(out[0][0], inter["z"][-1])
