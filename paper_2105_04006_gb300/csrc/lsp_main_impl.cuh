@@ -227,8 +227,8 @@ struct __align__(16) ObsF2 {
   uint32_t a_hi, b_hi, b_lo, kb_hi;  // phase words and the high word of K b
 };
 struct __align__(16) ObsF2W {
-  ObsF2 e;
-  f2_t w, nu, nw;     // {w, w} with w = 1 / dy^2, {-u, -u}, {-w, -w} (generalized periodogram)
+  ObsF2 e;            // e.y = {v, v} with v = u / sqrt(w) = sqrt(w) (y - ybar_w)
+  f2_t w, nu, nw;     // {r, r} with r = sqrt(w), w = 1 / dy^2; {-v, -v}; {-r, -r} (generalized periodogram)
 };
 
 __device__ __forceinline__ f2_t f2_dup(uint32_t v) { return f2_of(v, v); }
@@ -247,11 +247,19 @@ __device__ __forceinline__ void expand_obs(const uint4 r0, const uint4 r1, bool 
   e.b_lo = r1.y;
   e.kb_hi = K * r1.x + __umulhi(K, r1.y);  // high word of K b (mod 2^64)
 }
+// The generalized kernel runs its chains on sqrt(w) (cos, sin): the rotation
+// and the three-term steps are linear in the seeds, so scaled seeds give
+// scaled values c' = r c, s' = r s (r = sqrt(w)), and the six weighted sums
+// take one operation each: w c^2 = c'^2, w c s = c' s', w c = r c',
+// u c = (u / r) c' (and the same for s).
 __device__ __forceinline__ void expand_obs(const uint4 r0, const uint4 r1, bool cheb, uint32_t K, ObsF2W& e) {
   expand_obs(r0, r1, cheb, K, e.e);
-  e.w = f2_dup(r1.w);
-  e.nu = f2_dup(r0.x ^ 0x80000000u);
-  e.nw = f2_dup(r1.w ^ 0x80000000u);
+  const float r = sqrtf(__uint_as_float(r1.w));
+  const uint32_t v = __float_as_uint(__fdiv_rn(__uint_as_float(r0.x), r));
+  e.e.y = f2_dup(v);
+  e.w = f2_dup(__float_as_uint(r));
+  e.nu = f2_dup(v ^ 0x80000000u);
+  e.nw = f2_dup(__float_as_uint(r) ^ 0x80000000u);
 }
 
 // Stage records [0, nt) of src (32-byte RecF32, nt <= LSP_TILE_OBS) into
@@ -457,8 +465,10 @@ __global__ void __launch_bounds__(MAXT, MINB) main_f32_packed_floor(MainParams<R
 // ------------------------------------------------------------------------
 // Generalized periodogram (Section 4.11), FP32, two packed reseed chains:
 // the same tiling and seeding as main_f32_packed with six weighted sums per
-// frequency (11 FP32 operations per pair instead of 8).  Records carry
-// u = w (y - ybar_w) in the y word and w in the spare word.
+// frequency (11 FP32 operations per pair instead of 8 in the rotation form;
+// the kernel spends 8: two for the three-term step and one per sum, its
+// chains carrying sqrt(w) (cos, sin)).  Records carry u = w (y - ybar_w) in
+// the y word and w in the spare word.
 template <int K>
 __global__ void __launch_bounds__(256) main_f32_packed_gls(MainParams<RecF32, float> p) {
   constexpr int F = 2 * K;
@@ -503,17 +513,18 @@ __global__ void __launch_bounds__(256) main_f32_packed_gls(MainParams<RecF32, fl
         const ObsF2& e = ew.e;
         f2_t c2, s2;
         seed_pair_kb(e, k0, c2, s2);
-        const f2_t u2 = e.y, nu2 = ew.nu, w2 = ew.w, nw2 = ew.nw;
+        const f2_t v2 = e.y, nv2 = ew.nu, r2 = ew.w, nr2 = ew.nw;
+        c2 = f2_mul(r2, c2);  // chains of sqrt(w) (cos, sin)
+        s2 = f2_mul(r2, s2);
         chain3_mode<K, decltype(cheb_tag)::value>(c2, s2, e.cr, e.sr, e.nsr, e.coef, e.ncoef,
                                                   [&](int m, bool neg, f2_t c, f2_t s) {
-                                                    const f2_t uu = neg ? nu2 : u2, ww = neg ? nw2 : w2;
-                                                    xc[m] = f2_fma(uu, c, xc[m]);
-                                                    xs[m] = f2_fma(uu, s, xs[m]);
-                                                    cw[m] = f2_fma(ww, c, cw[m]);
-                                                    sw[m] = f2_fma(ww, s, sw[m]);
-                                                    const f2_t wc = f2_mul(w2, c);
-                                                    cc[m] = f2_fma(wc, c, cc[m]);
-                                                    cs[m] = f2_fma(wc, s, cs[m]);
+                                                    const f2_t vv = neg ? nv2 : v2, rr = neg ? nr2 : r2;
+                                                    xc[m] = f2_fma(vv, c, xc[m]);
+                                                    xs[m] = f2_fma(vv, s, xs[m]);
+                                                    cw[m] = f2_fma(rr, c, cw[m]);
+                                                    sw[m] = f2_fma(rr, s, sw[m]);
+                                                    cc[m] = f2_fma(c, c, cc[m]);
+                                                    cs[m] = f2_fma(c, s, cs[m]);
                                                   });
       };
       // (the accumulator flip of main_f32_packed costs this kernel registers
