@@ -621,21 +621,31 @@ __global__ void __launch_bounds__(256) main_f64_gls(MainParams<RecF64, double> p
       const uint4* src = reinterpret_cast<const uint4*>(p.rec + ts);
       for (int i = tid; i < 3 * nt; i += blockDim.x) s_rec[i] = __ldg(src + i);
       __syncthreads();
+      // chains of sqrt(w) (cos, sin), as in main_f32_packed_gls: the staged
+      // record holds v = u / sqrt(w) in the y word and sqrt(w) in the spare word
+      for (int i = tid; i < nt; i += blockDim.x) {
+        RecF64* q = reinterpret_cast<RecF64*>(s_rec) + i;
+        const double r = sqrt(__longlong_as_double((long long)q->pad));
+        q->y = q->y / r;
+        q->pad = (uint64_t)__double_as_longlong(r);
+      }
+      __syncthreads();
       const int nt_c = (int64_t)k0 < p.n_f ? nt : 0;  // bins past the grid end: staging only
       for (int j = 0; j < nt_c; ++j) {
         const RecF64 r = srec[j];
         double c, s;
         seed_sincos_f64(r.a + (uint64_t)k0 * r.b, c, s);
-        const double u = r.y, w = __longlong_as_double((long long)r.pad), nu = neg_(u), nw = neg_(w);
+        const double v = r.y, rw = __longlong_as_double((long long)r.pad), nv = neg_(v), nrw = neg_(rw);
+        c *= rw;
+        s *= rw;
         chain3<K>(c, s, r.cr, r.sr, sin_dominates(r.cr, r.sr), [&](int m, bool neg, double cm, double sm) {
-          const double uu = neg ? nu : u, ww = neg ? nw : w;
-          xc[m] = fma(uu, cm, xc[m]);
-          xs[m] = fma(uu, sm, xs[m]);
-          cw[m] = fma(ww, cm, cw[m]);
-          sw[m] = fma(ww, sm, sw[m]);
-          const double wc = w * cm;
-          cc[m] = fma(wc, cm, cc[m]);
-          cs[m] = fma(wc, sm, cs[m]);
+          const double vv = neg ? nv : v, rr = neg ? nrw : rw;
+          xc[m] = fma(vv, cm, xc[m]);
+          xs[m] = fma(vv, sm, xs[m]);
+          cw[m] = fma(rr, cm, cw[m]);
+          sw[m] = fma(rr, sm, sw[m]);
+          cc[m] = fma(cm, cm, cc[m]);
+          cs[m] = fma(cm, sm, cs[m]);
         });
       }
       __syncthreads();
