@@ -115,3 +115,14 @@ def test_clock_sampler_waits_for_the_first_sample(monkeypatch):
     got = clk.stop()
     assert got["sm_mhz"] == 2070.0 and got["sm_max_mhz"] == 2070.0
     assert got["reasons"] == ["sw_power_cap"] and got["power_w_max"] == 500.0
+
+
+def test_mlp_mode_has_no_reference_arm():
+    # --mlp times the library's tensor-core GEMMs; its reference arm says so in one JSON line
+    import json
+    import subprocess
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--mlp", "--impl", "reference"],
+                         capture_output=True, text=True, timeout=120, cwd=ROOT)
+    assert out.returncode == 0, out.stderr[-2000:]
+    line = json.loads(out.stdout.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and "unavailable" in line
