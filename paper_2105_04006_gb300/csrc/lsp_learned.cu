@@ -50,20 +50,27 @@ size_t align256(size_t x) { return (x + 255) / 256 * 256; }
 // lag_max, four candidates per step; otherwise all n^2 candidate pairs are
 // scanned in flat blocks of 1024.  Pairs with |t_j - t_i| < lag_max go to a
 // shared buffer in scan order (a block-wide prefix sum keeps the order, and so
-// the float sums, deterministic).  Thread c then adds w cos(2 pi f_c dt) for
-// every buffered pair to coarse bin c; the lag histogram counts pairs per lag
+// the float sums, deterministic).  Warp w then takes buffered pairs w, w + 8,
+// ...; lane l adds w cos(2 pi f_c dt) of each to coarse bins 8l .. 8l + 7:
+// two cosines from the SFU (bins 8l and 8l + 1, the second one grid step of
+// phase after the first) and the other six from the three-term recurrence
+// cos(x + d) = 2 cos(d) cos(x) - cos(x - d), whose error grows at most
+// linearly over the six steps.  The eight warps' partial sums of each bin are
+// added in warp order at the end.  The lag histogram counts pairs per lag
 // bin.
 constexpr int kFeatThreads = 256;
 constexpr int kCoarse = 256;
 constexpr int kLagBins = 256;
 constexpr int kPairBlock = 4 * kFeatThreads;
+constexpr int kBinsPerLane = kCoarse / 32;
+static_assert(kBinsPerLane == 8, "the featurizer's lanes take eight coarse bins each");
 
-__global__ void __launch_bounds__(kFeatThreads) featurize_kernel(
+__global__ void __launch_bounds__(kFeatThreads, 6) featurize_kernel(
     const double* __restrict__ t, const float* __restrict__ y, const int64_t* __restrict__ offsets,
     int64_t total_nt, double f_min, double f_max, float lag_max, bf16* __restrict__ feat16,
     float* __restrict__ feat32) {
-  __shared__ float s_dt[kPairBlock];
-  __shared__ float s_w[kPairBlock];
+  __shared__ float4 s_pair[kPairBlock];  // dt, weight, grid step of phase (cycles), 2 cos(step)
+  __shared__ float s_part[kFeatThreads / 32][kCoarse];
   __shared__ uint32_t s_hist[kLagBins];
   __shared__ int s_scan[kFeatThreads / 32];
   __shared__ double s_red[32];
@@ -96,9 +103,13 @@ __global__ void __launch_bounds__(kFeatThreads) featurize_kernel(
   var = n > 0 ? var / n : 0.0;
   const bool ok = n >= 2 && var > 0.0;
   const float rstd = ok ? (float)(1.0 / sqrt(var)) : 0.0f;
-  const float fc = (float)(f_min + (tid + 0.5) * (f_max - f_min) / kCoarse);
+  constexpr float kTwoPi = 6.28318530717958647692f;
+  const float fc0 = (float)(f_min + (kBinsPerLane * lane + 0.5) * (f_max - f_min) / kCoarse);
+  const float dfc = (float)((f_max - f_min) / kCoarse);
   const float lag_scale = kLagBins / lag_max;
-  float acc = 0.0f;
+  float acc8[kBinsPerLane];
+#pragma unroll
+  for (int k = 0; k < kBinsPerLane; ++k) acc8[k] = 0.0f;
   uint32_t n_pairs = 0u;
   // time-sorted light curves (the usual case) only need the short-lag band
   // after each observation; others are scanned over all n^2 candidates
@@ -123,17 +134,30 @@ __global__ void __launch_bounds__(kFeatThreads) featurize_kernel(
     }
     const int at = wbase + incl - cnt;
     for (int q = 0; q < cnt; ++q) {
-      s_dt[at + q] = dt[q];
-      s_w[at + q] = w[q];
+      const float pb = dfc * dt[q];  // one grid step of phase, cycles
+      const float step = pb - rintf(pb);
+      s_pair[at + q] = make_float4(dt[q], w[q], step, 2.0f * __cosf(kTwoPi * step));
       int lb = (int)(dt[q] * lag_scale);
       lb = lb < kLagBins - 1 ? lb : kLagBins - 1;
       atomicAdd(&s_hist[lb], 1u);
     }
     __syncthreads();
-    for (int q = 0; q < total; ++q) {
-      const float ph = fc * s_dt[q];  // cycles; |ph| < 12 * 16
-      const float x = ph - rintf(ph);
-      acc = fmaf(s_w[q], __cosf(6.28318530717958647692f * x), acc);
+    for (int q = warp; q < total; q += kFeatThreads / 32) {
+      const float4 pr = s_pair[q];
+      const float ph = fc0 * pr.x;  // cycles; |ph| < 12 * 16
+      const float x0 = ph - rintf(ph);
+      float x1 = x0 + pr.z;
+      x1 -= rintf(x1);
+      float cm = __cosf(kTwoPi * x0), c = __cosf(kTwoPi * x1);
+      acc8[0] = fmaf(pr.y, cm, acc8[0]);
+      acc8[1] = fmaf(pr.y, c, acc8[1]);
+#pragma unroll
+      for (int k = 2; k < kBinsPerLane; ++k) {
+        const float cn = fmaf(pr.w, c, -cm);
+        cm = c;
+        c = cn;
+        acc8[k] = fmaf(pr.y, c, acc8[k]);
+      }
     }
     n_pairs += (uint32_t)total;
     __syncthreads();
@@ -186,6 +210,11 @@ __global__ void __launch_bounds__(kFeatThreads) featurize_kernel(
       flush(cnt, dt, w);
     }
   }
+#pragma unroll
+  for (int k = 0; k < kBinsPerLane; ++k) s_part[warp][kBinsPerLane * lane + k] = acc8[k];
+  __syncthreads();
+  float acc = 0.0f;
+  for (int ww = 0; ww < kFeatThreads / 32; ++ww) acc += s_part[ww][tid];
   const float f_c = ok ? acc / (float)(n_pairs + 1u) : 0.0f;
   const float f_l = ok ? log1pf((float)s_hist[tid]) : 0.0f;
   feat16[o * LSP_FEAT_DIM + tid] = __float2bfloat16_rn(f_c);
