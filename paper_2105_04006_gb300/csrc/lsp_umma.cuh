@@ -15,11 +15,14 @@
 //   * warp 2 allocates and frees the tensor memory;
 //   * all four warps then read the accumulator back with tcgen05.ld (warp w
 //     owns tile rows 32w..32w+31, one row per thread), add the bias, apply
-//     ReLU, and stage the FP32 tile in the idle ring; the stores to global
-//     memory then run along rows (or, for the transposed copy, along
-//     columns) so that each warp writes contiguous bytes: multiplication by
-//     a ReLU mask, FP32 and/or bfloat16 outputs, and an optional transposed
-//     bfloat16 copy (the operand layout the weight-gradient GEMM reads).
+//     ReLU, and stage the FP32 tile in the idle ring, 128 columns at a time;
+//     the stores to global memory then run along rows, 8 columns per lane
+//     with 16-byte writes (or, for the transposed copy, down columns), so
+//     that each warp writes contiguous bytes: multiplication by a ReLU mask,
+//     FP32 and/or bfloat16 outputs, and an optional transposed bfloat16 copy
+//     (the operand layout the weight-gradient GEMM reads).
+// Two CTAs share an SM (99 KiB of shared memory and 256 TMEM columns each),
+// so one CTA's epilogue overlaps the other's loads and MMAs.
 // Rows and columns outside the matrices are zero-filled by TMA, so any M, N,
 // K work; the operands need 16-byte-aligned bases and row pitches.
 //
@@ -38,7 +41,7 @@ typedef __nv_bfloat16 bf16;
 
 constexpr int BM = 128;      // tile rows (tcgen05 M)
 constexpr int BK = 64;       // K slice per stage: 64 bfloat16 = one 128-byte swizzle row
-constexpr int STAGES = 2;  // two CTAs share an SM: one's epilogue overlaps the other's loads
+constexpr int STAGES = 2;    // two CTAs share an SM: one's epilogue overlaps the other's loads
 constexpr int MAX_BN = 256;  // tcgen05 N limit for M = 128
 constexpr int THREADS = 128;
 constexpr int TMEM_COLS = 256;
